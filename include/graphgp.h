@@ -1,0 +1,203 @@
+/*
+ * graphgp.h -- C ABI of the GB300 GraphGP library (Vecchia approximation of a
+ * Gaussian process on an arbitrary 3-D point cloud).
+ *
+ * Method: "GraphGP: Scalable Gaussian Processes with Vecchia's Approximation".
+ * Citations below name the paper's section, equation or algorithm.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Pointers ending in _d are DEVICE pointers on the current CUDA device;
+ *    pointers ending in _h are HOST pointers.  The caller owns every buffer it
+ *    passes; the library never frees or retains them after the call returns.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Every call is stream-ordered.  Calls that must read a device
+ *    value on the host (graph build, status queries, save) synchronise
+ *    `stream` and say so.
+ *  - Handles (graphgp_graph_t, graphgp_factor_t) own device memory allocated
+ *    with the stream-ordered allocator on the stream given at creation, until
+ *    the matching *_destroy call.  A handle may be used on any stream, but
+ *    calls that use one handle must not overlap on the device.
+ *  - Vectors (xi, v and their cotangents) are float[N] in GRAPH ORDER: the
+ *    depth-sorted generation order of Sec. 2.2 ("Batch construction").
+ *    order[pos] gives the input index of the point at position pos.
+ *  - Every call returns a graphgp_status.  Argument errors are reported
+ *    before any work is enqueued and leave outputs untouched.  Errors found on
+ *    the device (a bounded wait that timed out, a non-positive pivot) are
+ *    recorded in the handle and returned by graphgp_sync_status.
+ *  - Sizes: 1 <= k <= 32 neighbours, d == 3, k <= n0 <= N, n0 <= 2048,
+ *    N < 2^31.
+ */
+#ifndef GRAPHGP_H
+#define GRAPHGP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct graphgp_graph_s* graphgp_graph_t;
+typedef struct graphgp_factor_s* graphgp_factor_t;
+
+typedef enum {
+  GRAPHGP_OK = 0,
+  GRAPHGP_ERR_INVALID = -1, /* bad argument or size */
+  GRAPHGP_ERR_OOM = -2,     /* device allocation failed */
+  GRAPHGP_ERR_CUDA = -3,    /* a CUDA runtime call failed */
+  GRAPHGP_ERR_TIMEOUT = -4, /* a bounded device wait gave up */
+  GRAPHGP_ERR_NAN = -5,     /* non-finite input coordinates */
+  GRAPHGP_ERR_IO = -6,      /* file could not be read or written */
+  GRAPHGP_WARN_NOT_PD = 1   /* some pivots were clamped (Sec. 2.1, Eq. 2) */
+} graphgp_status;
+
+/* Stationary covariance kappa(r) (Sec. 2.1).  Matern with half-integer
+ * smoothing nu in {1/2, 3/2, 5/2} in closed form, and the squared
+ * exponential.  The nugget is added to K_ii only (same point, never to two
+ * distinct coincident points). */
+typedef enum {
+  GRAPHGP_MATERN12 = 0, /* s2 * exp(-r/l)                                   */
+  GRAPHGP_MATERN32 = 1, /* s2 * (1 + sqrt3 r/l) exp(-sqrt3 r/l)             */
+  GRAPHGP_MATERN52 = 2, /* s2 * (1 + sqrt5 r/l + 5r^2/(3l^2)) exp(-sqrt5 r/l) */
+  GRAPHGP_SQEXP = 3     /* s2 * exp(-r^2/(2 l^2))                           */
+} graphgp_kernel_type;
+
+typedef struct {
+  int32_t type;       /* graphgp_kernel_type */
+  int32_t reserved;   /* must be 0 */
+  double sigma2;      /* marginal variance s2 > 0 */
+  double lengthscale; /* l > 0 */
+  double nugget;      /* >= 0, added on the diagonal */
+} graphgp_kernel;
+
+typedef struct {
+  int32_t n0;         /* size of the dense initial block (Sec. 2.2, Alg. 1
+                         line "dense initial batch"); 0 = default
+                         min(N, max(k, 256)) */
+  int32_t split_rule; /* k-d split dimension: 0 = widest bounding-box extent
+                         (ties to the lowest dimension), 1 = level mod 3 */
+  int64_t max_spin;   /* bound on device spin iterations; 0 = default */
+} graphgp_build_opts;
+
+/* ---- graph construction (Sec. 2.2, Sec. 2.3 last paragraph) ------------
+ * Builds the bit-reversed left-balanced k-d tree over points_d (float[N][3],
+ * input order), the k nearest PRECEDING neighbours of every point with tree
+ * index >= n0 (key: FP32 squared distance, ties to the lower tree index),
+ * the depth of every point (d_i = 1 + max over c(i), dense block = 0), and
+ * the depth-sorted graph order (ties by k-d tree in-order rank).
+ * Synchronises `stream` (the host needs the number of depth levels).
+ * Returns GRAPHGP_ERR_NAN for non-finite coordinates; -0.0 is read as +0.0. */
+int graphgp_build_graph(const float* points_d, int64_t N, int d, int k,
+                        const graphgp_build_opts* opts, void* stream,
+                        graphgp_graph_t* out);
+
+/* Creates a graph handle from host arrays that already hold a graph in graph
+ * order: points_h float[N][3] in INPUT order, order_h int32[N] (position ->
+ * input index), nbr_h int32[(N-n0)*k] (row pos-n0 holds the positions of
+ * c(pos), each < level_offsets[depth(pos)]), level_offsets_h
+ * int64[num_levels+1] with level_offsets_h[0] = 0, level_offsets_h[1] = n0,
+ * level_offsets_h[num_levels] = N.  Used by graphgp_graph_load.  Validates
+ * every index; synchronises `stream`. */
+int graphgp_graph_import(const float* points_h, int64_t N, int k, int n0,
+                         const int32_t* order_h, const int32_t* nbr_h,
+                         const int64_t* level_offsets_h, int num_levels,
+                         void* stream, graphgp_graph_t* out);
+
+/* num_levels counts depth levels including the dense level 0, so the
+ * level_offsets array has num_levels+1 entries.  bytes = device bytes held. */
+int graphgp_graph_info(graphgp_graph_t g, int64_t* N, int* k, int* n0,
+                       int* num_levels, size_t* bytes);
+
+/* Copies the graph out.  order_d int32[N], nbr_d int32[(N-n0)*k] (positions,
+ * nearest first), level_offsets_h int64[num_levels+1].  Any pointer may be
+ * NULL to skip it.  Synchronises `stream` when level_offsets_h != NULL. */
+int graphgp_graph_export(graphgp_graph_t g, int32_t* order_d, int32_t* nbr_d,
+                         int64_t* level_offsets_h, void* stream);
+
+/* Copies the k-d tree out (only for graphs made by graphgp_build_graph):
+ * tree_point_d int32[N] (tree index -> input index), split_dim_d uint8[N],
+ * inorder_d int32[N] (tree index -> in-order rank), depth_d int32[N] (tree
+ * index -> depth), nbr_tree_d int32[(N-n0)*k] (tree index j >= n0 -> tree
+ * indices of c(j), nearest first).  Any pointer may be NULL.  Fails with
+ * GRAPHGP_ERR_INVALID if the tree arrays were released. */
+int graphgp_graph_export_tree(graphgp_graph_t g, int32_t* tree_point_d,
+                              uint8_t* split_dim_d, int32_t* inorder_d,
+                              int32_t* depth_d, int32_t* nbr_tree_d,
+                              void* stream);
+
+/* Versioned binary checkpoint of a graph (points, order, neighbours, level
+ * offsets).  Save synchronises `stream`. */
+int graphgp_graph_save(graphgp_graph_t g, const char* path, void* stream);
+int graphgp_graph_load(const char* path, void* stream, graphgp_graph_t* out);
+
+void graphgp_graph_destroy(graphgp_graph_t g);
+
+/* ---- factor (Sec. 2.1, Eq. 2; Alg. 1) -----------------------------------
+ * For every position i >= n0: K_cc, K_ci from kappa on the coordinates of
+ * c(i) and i, L = chol(K_cc), y = L^-1 K_ci, b_i = L^-T y (the weights
+ * K_ic K_cc^-1 of Eq. 2), sigma_i^2 = K_ii - y.y (compensated FP32),
+ * sigma_i = sqrt.  Dense block: L0 = chol(K_00) over positions 0..n0-1 and
+ * its inverse, sigma_i = L0_ii.  logdet = 2 sum_i log sigma_i is reduced in
+ * FP64 from the stored FP32 sigma.  Pivots below 1e-7 * K_jj are clamped to
+ * that value and counted (see graphgp_sync_status). */
+int graphgp_factor(graphgp_graph_t g, const graphgp_kernel* kern, void* stream,
+                   graphgp_factor_t* out);
+
+/* b_d float[(N-n0)*k] (row-major, same neighbour order as the graph),
+ * sigma_d float[N], L0_d float[n0*n0] (row-major, lower triangle, upper
+ * entries zero).  Any pointer may be NULL. */
+int graphgp_factor_export(graphgp_factor_t f, float* b_d, float* sigma_d,
+                          float* L0_d, void* stream);
+
+void graphgp_factor_destroy(graphgp_factor_t f);
+
+/* Synchronises `stream`, then reports device-side conditions recorded in the
+ * handles (either may be NULL): GRAPHGP_ERR_TIMEOUT if a bounded wait gave
+ * up, else GRAPHGP_WARN_NOT_PD if the factor clamped pivots, else OK.
+ * n_not_pd (nullable) receives the number of clamped rows. */
+int graphgp_sync_status(graphgp_graph_t g, graphgp_factor_t f, void* stream,
+                        int64_t* n_not_pd);
+
+/* ---- sweeps (Alg. 1; Sec. 3 "inverse and log-determinant") --------------
+ * generate: v = L xi, i.e. v_0 = L0 xi_0, then level by level
+ *           v_i = b_i . v_c(i) + sigma_i xi_i.
+ * whiten:   xi = L^-1 v, i.e. xi_0 = L0^-1 v_0, xi_i = (v_i - b_i.v_c(i))/sigma_i.
+ * logdet:   out_d[0] = log det(L L^T) = 2 sum log sigma_i (double, device).
+ * nll:      out_d[0] = 0.5 xi.xi + 0.5 logdet with xi = whiten(v) (double). */
+int graphgp_generate(graphgp_graph_t g, graphgp_factor_t f, const float* xi_d,
+                     float* v_d, void* stream);
+int graphgp_whiten(graphgp_graph_t g, graphgp_factor_t f, const float* v_d,
+                   float* xi_d, void* stream);
+int graphgp_logdet(graphgp_factor_t f, double* out_d, void* stream);
+int graphgp_nll(graphgp_graph_t g, graphgp_factor_t f, const float* v_d,
+                double* out_d, void* stream);
+
+/* ---- adjoints (Sec. 2.3 "forward and backward derivatives") -------------
+ * Vector-Jacobian products.  thetabar_d is double[3] =
+ * [d/d lengthscale, d/d sigma2, d/d nugget] and is ACCUMULATED (+=).  The
+ * per-point factors are recomputed, not stored.
+ * generate_backward: given vbar = dL/dv for v = generate(xi), writes
+ *   xibar_d (overwritten) and adds the kernel-parameter gradient.
+ * whiten_backward: given xibar = dL/dxi for xi = whiten(v) and a scalar
+ *   logdetbar = dL/dlogdet, writes vbar_d (overwritten) and adds thetabar.
+ * nll_backward: gradient of nll(v) times nllbar: vbar_d, thetabar_d. */
+int graphgp_generate_backward(graphgp_graph_t g, graphgp_factor_t f,
+                              const float* xi_d, const float* v_d,
+                              const float* vbar_d, float* xibar_d,
+                              double* thetabar_d, void* stream);
+int graphgp_whiten_backward(graphgp_graph_t g, graphgp_factor_t f,
+                            const float* v_d, const float* xi_d,
+                            const float* xibar_d, double logdetbar,
+                            float* vbar_d, double* thetabar_d, void* stream);
+int graphgp_nll_backward(graphgp_graph_t g, graphgp_factor_t f,
+                         const float* v_d, double nllbar, float* vbar_d,
+                         double* thetabar_d, void* stream);
+
+const char* graphgp_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GRAPHGP_H */
