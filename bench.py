@@ -1,0 +1,311 @@
+#!/usr/bin/env python3
+"""Benchmark of the GraphGP Vecchia hot path on GB300.
+
+One step = one generate sweep (v = L xi, Alg. 1) + one whiten sweep
+(xi = L^-1 v, Sec. 3) + the log-determinant, over the whole headline
+workload: N = 2^26 points from a 3-D unit Gaussian (the paper's benchmark
+cloud), k = 16 preceding neighbours, Matern-3/2 (s2 = 1, l = 0.1, nugget
+1e-6), n0 = 256.  The graph and the factor are built once before timing
+(their throughput is reported beside the line).  Every operand (4 GiB of
+neighbour rows, 4 GiB of weights, 256 MiB per vector) is larger than the
+129 MB L2, so no flush is needed between steps.
+
+value = points per second through one step (N / step time).
+e2e   = the same through the public API from pinned HOST buffers: xi copied
+        in, v and xi and logdet copied out, inside the timed region.
+
+Multi-GPU: the path does not shard (one instance per GPU); under torchrun
+every rank runs an independent replica and value sums the ranks' points
+over the slowest rank's time ("replicas only", weak scaling).
+
+--impl reference times the FP64 CPU oracle (the reference arm of this
+project) on a bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "generate/whiten points/s at N=2^26,k=16 (%HBM peak); serving p50/p99 latency"
+UNIT = "points/s"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _clock_sampler(out_path):
+    q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    try:
+        f = open(out_path, "w")
+        return subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                 "-lms", "200"], stdout=f, stderr=subprocess.DEVNULL), f
+    except Exception:
+        return None, None
+
+
+def _clock_summary(path, gpu_index):
+    sm, mx, reasons = [], None, set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    try:
+        for line in open(path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9 or parts[0] != str(gpu_index):
+                continue
+            sm.append(float(parts[1]))
+            mx = float(parts[2])
+            for n, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(n)
+    except Exception:
+        pass
+    if not sm:
+        return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": ["unsampled"]}
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+            "samples": len(sm)}
+
+
+def cpu_baseline(N_sample=1 << 18, reps=10):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload."""
+    import numpy as np
+    import oracle
+    import workloads
+    w = workloads.WORKLOADS["metric"]
+    pts = workloads.unit_gaussian(N_sample, w["seed"])
+    t0 = time.perf_counter()
+    g = oracle.build_graph(pts, w["k"], 256, knn="tree")
+    t_graph = time.perf_counter() - t0
+    K = oracle.Kernel(*w["kernel"])
+    t0 = time.perf_counter()
+    fo = oracle.factor(g["pts_pos"], g["nbr_pos"], w["k"], 256, K)
+    t_factor = time.perf_counter() - t0
+    xi = workloads.white_noise(N_sample, w["xi_seed"]).astype(np.float64)
+    times = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        v = oracle.generate(fo, g["nbr_pos"], w["k"], 256, xi)
+        oracle.whiten(fo, g["nbr_pos"], w["k"], 256, v)
+        oracle.logdet(fo["sigma"])
+        times.append(time.perf_counter() - t0)
+    t_step = statistics.median(times)
+    return {"value": N_sample / t_step, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"unit-Gaussian cloud of {N_sample} points, k={w['k']}, n0=256, same kernel; "
+                       f"median of {reps} generate+whiten+logdet passes (FP64, 1 thread); "
+                       f"oracle graph build {t_graph:.1f} s and factor {t_factor:.1f} s untimed"),
+            "ms_per_step": t_step * 1e3,
+            "graph_points_per_s": N_sample / t_graph, "factor_points_per_s": N_sample / t_factor}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    reps = max(1, args.steps)
+    cb = cpu_baseline(reps=reps + args.warmup)
+    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": cb["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "metric: unit Gaussian 3-D, N=2^26 (sampled), k=16, "
+                                   "Matern-3/2 l=0.1 nugget 1e-6, n0=256"},
+            "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
+            "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_2606_11402_gb300 as gg
+    import workloads
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = world > 1
+    if dist:
+        import torch.distributed as td
+        td.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    gg.load()
+    w = dict(workloads.WORKLOADS["metric"])
+    if args.N:
+        w["N"] = args.N
+    N, k = w["N"], w["k"]
+    kern = gg.Kernel(*w["kernel"])
+    stream = torch.cuda.current_stream()
+
+    pts = torch.from_numpy(workloads.unit_gaussian(N, w["seed"] + rank)).cuda()
+    xi_h = workloads.white_noise(N, w["xi_seed"] + rank)
+    xi = torch.from_numpy(xi_h).cuda()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g = gg.build_graph(pts, k, n0=256)
+    torch.cuda.synchronize()
+    t_graph = time.perf_counter() - t0
+    del pts
+    t0 = time.perf_counter()
+    f = gg.factor(g, kern)
+    torch.cuda.synchronize()
+    t_factor = time.perf_counter() - t0
+    st, nbad = gg.sync_status(g, f)
+    v = torch.empty_like(xi)
+    xo = torch.empty_like(xi)
+    ld = torch.empty(1, dtype=torch.float64, device="cuda")
+
+    def step():
+        gg.generate(g, f, xi, out=v)
+        gg.whiten(g, f, v, out=xo)
+        gg.logdet(f, out=ld)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    # per-sweep timing on the launching stream
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    sampler, sf = _clock_sampler(os.path.join("/tmp", f"ggp_clocks_{rank}.csv"))
+    time.sleep(0.3 if sampler else 0)
+    if dist:
+        td.barrier()
+    torch.cuda.synchronize()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for e0, e1, e2 in ev:
+        e0.record(stream)
+        gg.generate(g, f, xi, out=v)
+        e1.record(stream)
+        gg.whiten(g, f, v, out=xo)
+        e2.record(stream)
+        gg.logdet(f, out=ld)
+    end.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        td.barrier()
+    if sampler:
+        time.sleep(0.2)
+        sampler.terminate()
+        sampler.wait()
+        sf.close()
+    total_ms = start.elapsed_time(end)
+    gen_ms = statistics.mean(a.elapsed_time(b) for a, b, _ in ev)
+    wh_ms = statistics.mean(b.elapsed_time(c) for _, b, c in ev)
+    t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+    if dist:
+        td.all_reduce(t, op=td.ReduceOp.MAX)
+    ms_step = t.item() / args.steps
+    value = N * world / (ms_step / 1e3)
+    st2, _ = gg.sync_status(g, f)
+    assert st2 >= 0
+
+    # end to end through the public API with pinned host buffers
+    xi_pin = torch.from_numpy(xi_h).pin_memory()
+    v_pin = torch.empty(N, dtype=torch.float32).pin_memory()
+    xo_pin = torch.empty(N, dtype=torch.float32).pin_memory()
+    ld_pin = torch.empty(1, dtype=torch.float64).pin_memory()
+    xi_d = torch.empty_like(xi)
+
+    def e2e_step():
+        xi_d.copy_(xi_pin, non_blocking=True)
+        gg.generate(g, f, xi_d, out=v)
+        gg.whiten(g, f, v, out=xo)
+        gg.logdet(f, out=ld)
+        v_pin.copy_(v, non_blocking=True)
+        xo_pin.copy_(xo, non_blocking=True)
+        ld_pin.copy_(ld, non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    s2, e2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s2.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e2.record(stream)
+    torch.cuda.synchronize()
+    t2 = torch.tensor([s2.elapsed_time(e2)], device="cuda", dtype=torch.float64)
+    if dist:
+        td.all_reduce(t2, op=td.ReduceOp.MAX)
+    e2e_ms = t2.item() / args.steps
+    assert np.isfinite(v_pin.numpy()).all()
+
+    hbm, peak_kind = _peaks()
+    rows = N - g.n0
+    bytes_per_point = 8 * k + 16
+    alg_bytes = rows * bytes_per_point
+    dom = "generate" if gen_ms >= wh_ms else "whiten"
+    dom_ms = max(gen_ms, wh_ms)
+    achieved = alg_bytes / (dom_ms / 1e3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": ("metric: unit Gaussian 3-D cloud, N=2^26, k=16, Matern-3/2 "
+                                "s2=1 l=0.1 nugget 1e-6, n0=256; step = generate + whiten + logdet"),
+                   "N": N, "k": k, "n0": g.n0, "levels": g.num_levels,
+                   "l2": "inputs larger than L2 (no flush)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm,
+                     "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                     "peak_kind": peak_kind,
+                     "bytes_per_point": bytes_per_point, "points_per_launch": rows},
+        "stages": {"generate_ms": gen_ms, "whiten_ms": wh_ms,
+                   "generate_points_per_s": N / (gen_ms / 1e3),
+                   "whiten_points_per_s": N / (wh_ms / 1e3),
+                   "generate_hbm_frac": alg_bytes / (gen_ms / 1e3) / 1e9 / hbm,
+                   "whiten_hbm_frac": alg_bytes / (wh_ms / 1e3) / 1e9 / hbm,
+                   "graph_build_s": t_graph, "graph_points_per_s": N / t_graph,
+                   "factor_s": t_factor, "factor_points_per_s": N / t_factor,
+                   "not_pd_rows": nbad},
+        "e2e": {"value": N * world / (e2e_ms / 1e3), "unit": UNIT, "ms_per_step": e2e_ms,
+                "h2d_bytes_per_step": 4 * N, "d2h_bytes_per_step": 8 * N + 8},
+        "gpu_launches": 4 * args.steps,
+        "clocks": _clock_summary(os.path.join("/tmp", f"ggp_clocks_{rank}.csv"), local),
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = {kk: vv for kk, vv in cpu_baseline().items()
+                                if kk in ("value", "unit", "cores", "kind", "sample")}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        td.barrier()
+        td.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--N", type=int, default=0, help="override N (profiling a smaller case)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,330 @@
+"""GB300 GraphGP: Vecchia approximation of a Gaussian process on 3-D points.
+
+Thin Python binding of ``libgraphgp.so`` (C ABI in ``include/graphgp.h``):
+argument marshalling only.  Every step of the method runs in the library's
+CUDA kernels; there is no CPU or PyTorch fallback.  PyTorch provides device
+memory (tensors) and streams.
+
+Python names mirror the C entry points without the ``graphgp_`` prefix:
+``build_graph``, ``graph_import``, ``factor``, ``generate``, ``whiten``,
+``logdet``, ``nll`` and the ``*_backward`` adjoints.  Vectors are float32
+CUDA tensors in graph order (the depth-sorted generation order, Sec. 2.2).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgraphgp.so")
+
+MATERN12, MATERN32, MATERN52, SQEXP = 0, 1, 2, 3
+
+OK = 0
+ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_NAN, ERR_IO = -1, -2, -3, -4, -5, -6
+WARN_NOT_PD = 1
+
+
+class GraphGPError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {status_string(status)} ({status})")
+
+
+class _Kernel(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("sigma2", ctypes.c_double), ("lengthscale", ctypes.c_double),
+                ("nugget", ctypes.c_double)]
+
+
+class _BuildOpts(ctypes.Structure):
+    _fields_ = [("n0", ctypes.c_int32), ("split_rule", ctypes.c_int32),
+                ("max_spin", ctypes.c_int64)]
+
+
+@dataclass(frozen=True)
+class Kernel:
+    """Stationary covariance kappa(r) of Sec. 2.1 (Matern nu=1/2,3/2,5/2 or SE)."""
+    type: int = MATERN32
+    sigma2: float = 1.0
+    lengthscale: float = 0.1
+    nugget: float = 0.0
+
+    def _c(self) -> _Kernel:
+        return _Kernel(int(self.type), 0, float(self.sigma2), float(self.lengthscale),
+                       float(self.nugget))
+
+
+_lib = None
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_I = ctypes.c_int
+
+
+def load() -> ctypes.CDLL:
+    """Load libgraphgp.so; raises if it has not been built (no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(
+                f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                "(nvcc, sm_103a); the GraphGP path has no CPU fallback")
+        L = ctypes.CDLL(LIB_PATH)
+        sig = {
+            "graphgp_build_graph": [_P, _I64, _I, _I, _P, _P, _P],
+            "graphgp_graph_import": [_P, _I64, _I, _I, _P, _P, _P, _I, _P, _P],
+            "graphgp_graph_info": [_P, _P, _P, _P, _P, _P],
+            "graphgp_graph_export": [_P, _P, _P, _P, _P],
+            "graphgp_graph_export_tree": [_P, _P, _P, _P, _P, _P, _P],
+            "graphgp_graph_save": [_P, ctypes.c_char_p, _P],
+            "graphgp_graph_load": [ctypes.c_char_p, _P, _P],
+            "graphgp_factor": [_P, _P, _P, _P],
+            "graphgp_factor_export": [_P, _P, _P, _P, _P],
+            "graphgp_sync_status": [_P, _P, _P, _P],
+            "graphgp_generate": [_P, _P, _P, _P, _P],
+            "graphgp_whiten": [_P, _P, _P, _P, _P],
+            "graphgp_logdet": [_P, _P, _P],
+            "graphgp_nll": [_P, _P, _P, _P, _P],
+            "graphgp_generate_backward": [_P, _P, _P, _P, _P, _P, _P, _P],
+            "graphgp_whiten_backward": [_P, _P, _P, _P, _P, ctypes.c_double, _P, _P, _P],
+            "graphgp_nll_backward": [_P, _P, _P, ctypes.c_double, _P, _P, _P],
+        }
+        for name, args in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = ctypes.c_int
+        for name in ("graphgp_graph_destroy", "graphgp_factor_destroy"):
+            f = getattr(L, name)
+            f.argtypes = [_P]
+            f.restype = None
+        L.graphgp_status_string.argtypes = [_I]
+        L.graphgp_status_string.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def status_string(status: int) -> str:
+    return load().graphgp_status_string(status).decode()
+
+
+def _check(rc: int, what: str) -> int:
+    if rc < 0:
+        raise GraphGPError(rc, what)
+    return rc
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dev(t: torch.Tensor, dtype, n=None, what="tensor") -> ctypes.c_void_p:
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+        raise TypeError(f"{what}: expected a contiguous CUDA {dtype} tensor")
+    if n is not None and t.numel() != n:
+        raise ValueError(f"{what}: expected {n} elements, got {t.numel()}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Graph:
+    """Owns a graphgp_graph_t (neighbour graph and depth levels in HBM)."""
+
+    def __init__(self, handle: ctypes.c_void_p):
+        self._h = handle
+        N, k, n0, nl, nb = _I64(), _I(), _I(), _I(), ctypes.c_size_t()
+        _check(load().graphgp_graph_info(handle, ctypes.byref(N), ctypes.byref(k),
+                                         ctypes.byref(n0), ctypes.byref(nl), ctypes.byref(nb)),
+               "graph_info")
+        self.N, self.k, self.n0, self.num_levels, self.bytes = N.value, k.value, n0.value, nl.value, nb.value
+
+    @property
+    def handle(self):
+        return self._h
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.graphgp_graph_destroy(self._h)
+            self._h = None
+
+    def export(self, stream=None):
+        """(order int32[N], nbr int32[N-n0, k], level_offsets int64[num_levels+1])."""
+        dev = torch.device("cuda")
+        order = torch.empty(self.N, dtype=torch.int32, device=dev)
+        nbr = torch.empty((self.N - self.n0, self.k), dtype=torch.int32, device=dev)
+        lo = (ctypes.c_int64 * (self.num_levels + 1))()
+        _check(load().graphgp_graph_export(self._h, _dev(order, torch.int32), _dev(nbr, torch.int32),
+                                           lo, _stream(stream)), "graph_export")
+        return order, nbr, torch.tensor(list(lo), dtype=torch.int64)
+
+    def export_tree(self, stream=None):
+        """(tree_point, split_dim, inorder, depth, nbr_tree) indexed by tree index."""
+        dev = torch.device("cuda")
+        N = self.N
+        tp = torch.empty(N, dtype=torch.int32, device=dev)
+        sd = torch.empty(N, dtype=torch.uint8, device=dev)
+        io = torch.empty(N, dtype=torch.int32, device=dev)
+        dp = torch.empty(N, dtype=torch.int32, device=dev)
+        nt = torch.empty((N - self.n0, self.k), dtype=torch.int32, device=dev)
+        _check(load().graphgp_graph_export_tree(self._h, _dev(tp, torch.int32), _dev(sd, torch.uint8),
+                                                _dev(io, torch.int32), _dev(dp, torch.int32),
+                                                _dev(nt, torch.int32), _stream(stream)),
+               "graph_export_tree")
+        return tp, sd, io, dp, nt
+
+    def save(self, path: str, stream=None):
+        _check(load().graphgp_graph_save(self._h, path.encode(), _stream(stream)), "graph_save")
+
+
+class Factor:
+    """Owns a graphgp_factor_t (weights b, sigma, dense block) for one kernel."""
+
+    def __init__(self, handle: ctypes.c_void_p, graph: Graph, kernel: Kernel):
+        self._h = handle
+        self.graph = graph  # keeps the graph alive
+        self.kernel = kernel
+
+    @property
+    def handle(self):
+        return self._h
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.graphgp_factor_destroy(self._h)
+            self._h = None
+
+    def export(self, stream=None):
+        g = self.graph
+        dev = torch.device("cuda")
+        b = torch.empty((g.N - g.n0, g.k), dtype=torch.float32, device=dev)
+        sigma = torch.empty(g.N, dtype=torch.float32, device=dev)
+        L0 = torch.empty((g.n0, g.n0), dtype=torch.float32, device=dev)
+        _check(load().graphgp_factor_export(self._h, _dev(b, torch.float32), _dev(sigma, torch.float32),
+                                            _dev(L0, torch.float32), _stream(stream)), "factor_export")
+        return b, sigma, L0
+
+
+# --- entry points ------------------------------------------------------------
+def build_graph(points: torch.Tensor, k: int, n0: int = 0, split_rule: int = 0,
+                max_spin: int = 0, stream=None) -> Graph:
+    """graphgp_build_graph: points float32[N, 3] on the GPU (input order)."""
+    if points.dim() != 2 or points.shape[1] != 3:
+        raise ValueError("points must be [N, 3]")
+    h = ctypes.c_void_p()
+    opts = _BuildOpts(int(n0), int(split_rule), int(max_spin))
+    _check(load().graphgp_build_graph(_dev(points, torch.float32), points.shape[0], 3, int(k),
+                                      ctypes.byref(opts), _stream(stream), ctypes.byref(h)),
+           "build_graph")
+    return Graph(h)
+
+
+def graph_import(points, k, n0, order, nbr, level_offsets, stream=None) -> Graph:
+    """graphgp_graph_import from host (numpy) arrays already in graph order."""
+    import numpy as np
+    pts = np.ascontiguousarray(points, dtype=np.float32)
+    order = np.ascontiguousarray(order, dtype=np.int32)
+    nbr = np.ascontiguousarray(nbr, dtype=np.int32)
+    lo = np.ascontiguousarray(level_offsets, dtype=np.int64)
+    h = ctypes.c_void_p()
+    _check(load().graphgp_graph_import(pts.ctypes.data, pts.shape[0], int(k), int(n0),
+                                       order.ctypes.data, nbr.ctypes.data, lo.ctypes.data,
+                                       len(lo) - 1, _stream(stream), ctypes.byref(h)),
+           "graph_import")
+    return Graph(h)
+
+
+def graph_load(path: str, stream=None) -> Graph:
+    h = ctypes.c_void_p()
+    _check(load().graphgp_graph_load(path.encode(), _stream(stream), ctypes.byref(h)), "graph_load")
+    return Graph(h)
+
+
+def factor(graph: Graph, kernel: Kernel, stream=None) -> Factor:
+    h = ctypes.c_void_p()
+    kc = kernel._c()
+    _check(load().graphgp_factor(graph.handle, ctypes.byref(kc), _stream(stream), ctypes.byref(h)),
+           "factor")
+    return Factor(h, graph, kernel)
+
+
+def sync_status(graph=None, fac=None, stream=None):
+    """Synchronise and return (status, n_not_pd)."""
+    n = ctypes.c_int64(0)
+    rc = load().graphgp_sync_status(graph.handle if graph else None, fac.handle if fac else None,
+                                    _stream(stream), ctypes.byref(n))
+    _check(rc, "sync_status")
+    return rc, n.value
+
+
+def generate(graph: Graph, fac: Factor, xi: torch.Tensor, out: torch.Tensor | None = None,
+             stream=None) -> torch.Tensor:
+    v = torch.empty_like(xi) if out is None else out
+    _check(load().graphgp_generate(graph.handle, fac.handle, _dev(xi, torch.float32, graph.N, "xi"),
+                                   _dev(v, torch.float32, graph.N, "v"), _stream(stream)), "generate")
+    return v
+
+
+def whiten(graph: Graph, fac: Factor, v: torch.Tensor, out: torch.Tensor | None = None,
+           stream=None) -> torch.Tensor:
+    xi = torch.empty_like(v) if out is None else out
+    _check(load().graphgp_whiten(graph.handle, fac.handle, _dev(v, torch.float32, graph.N, "v"),
+                                 _dev(xi, torch.float32, graph.N, "xi"), _stream(stream)), "whiten")
+    return xi
+
+
+def logdet(fac: Factor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    o = torch.empty(1, dtype=torch.float64, device="cuda") if out is None else out
+    _check(load().graphgp_logdet(fac.handle, _dev(o, torch.float64, 1), _stream(stream)), "logdet")
+    return o
+
+
+def nll(graph: Graph, fac: Factor, v: torch.Tensor, out: torch.Tensor | None = None,
+        stream=None) -> torch.Tensor:
+    o = torch.empty(1, dtype=torch.float64, device="cuda") if out is None else out
+    _check(load().graphgp_nll(graph.handle, fac.handle, _dev(v, torch.float32, graph.N, "v"),
+                              _dev(o, torch.float64, 1), _stream(stream)), "nll")
+    return o
+
+
+def generate_backward(graph, fac, xi, v, vbar, xibar=None, thetabar=None, stream=None):
+    """Returns (xibar, thetabar[3] += [dl, dsigma2, dnugget])."""
+    xb = torch.empty_like(xi) if xibar is None else xibar
+    tb = torch.zeros(3, dtype=torch.float64, device="cuda") if thetabar is None else thetabar
+    _check(load().graphgp_generate_backward(graph.handle, fac.handle,
+                                            _dev(xi, torch.float32, graph.N, "xi"),
+                                            _dev(v, torch.float32, graph.N, "v"),
+                                            _dev(vbar, torch.float32, graph.N, "vbar"),
+                                            _dev(xb, torch.float32, graph.N, "xibar"),
+                                            _dev(tb, torch.float64, 3, "thetabar"), _stream(stream)),
+           "generate_backward")
+    return xb, tb
+
+
+def whiten_backward(graph, fac, v, xi, xibar, logdetbar=0.0, vbar=None, thetabar=None,
+                    stream=None):
+    """Returns (vbar, thetabar[3] += ...)."""
+    vb = torch.empty_like(v) if vbar is None else vbar
+    tb = torch.zeros(3, dtype=torch.float64, device="cuda") if thetabar is None else thetabar
+    _check(load().graphgp_whiten_backward(graph.handle, fac.handle,
+                                          _dev(v, torch.float32, graph.N, "v"),
+                                          _dev(xi, torch.float32, graph.N, "xi"),
+                                          _dev(xibar, torch.float32, graph.N, "xibar"),
+                                          float(logdetbar),
+                                          _dev(vb, torch.float32, graph.N, "vbar"),
+                                          _dev(tb, torch.float64, 3, "thetabar"), _stream(stream)),
+           "whiten_backward")
+    return vb, tb
+
+
+def nll_backward(graph, fac, v, nllbar=1.0, vbar=None, thetabar=None, stream=None):
+    vb = torch.empty_like(v) if vbar is None else vbar
+    tb = torch.zeros(3, dtype=torch.float64, device="cuda") if thetabar is None else thetabar
+    _check(load().graphgp_nll_backward(graph.handle, fac.handle,
+                                       _dev(v, torch.float32, graph.N, "v"), float(nllbar),
+                                       _dev(vb, torch.float32, graph.N, "vbar"),
+                                       _dev(tb, torch.float64, 3, "thetabar"), _stream(stream)),
+           "nll_backward")
+    return vb, tb

@@ -1,0 +1,561 @@
+// Adjoints (Sec. 2.3: forward and backward derivatives of the conditioning
+// steps, differentiated through the Cholesky factor).
+//
+// With every sparse row written as v_i = b_i . v_c(i) + sigma_i xi_i:
+//  * whiten VJP (xi = L^-1 v, cotangent xibar, logdetbar), w_i = xibar_i/sigma_i:
+//      vbar_i = w_i - sum over children (j, a) of i of w_j b_ja   (transposed
+//      gather over the children CSR), bbar_i = -w_i v_c, sigbar_i =
+//      -w_i xi_i + 2 logdetbar / sigma_i;
+//  * generate VJP (v = L xi, cotangent vbar): u = (I - B)^-T vbar by a reverse
+//      level sweep, u_j = vbar_j + sum over children (i, a) of j of b_ia u_i;
+//      xibar_i = sigma_i u_i, bbar_i = u_i v_c, sigbar_i = u_i xi_i;
+//  * factor backward, per row, from b = K_cc^-1 K_ci and s = sigma^2:
+//      sbar = sigbar/(2 sigma), g = K_cc^-1 bbar, Kbar_cc = -g b^T + sbar b b^T,
+//      Kbar_ci = g - 2 sbar b, Kbar_ii = sbar, theta_bar += sum Kbar dK/dtheta.
+//    The factors are recomputed (bit-identical to the forward), not stored.
+//  * dense block (L0 = chol(K_00)): Lbar0 from the sweep, then
+//      Kbar_00 = L0^-T Phi(L0^T Lbar0) L0^-1 (Phi: lower triangle, halved
+//      diagonal), theta_bar += sum Kbar_00 dK_00/dtheta.
+// theta = (lengthscale, sigma2, nugget); theta_bar is accumulated in FP64.
+#include <algorithm>
+
+#include "pointfactor.cuh"
+
+namespace ggp {
+namespace {
+
+__device__ __forceinline__ uint32_t ld_acq(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_rel(uint32_t* p, uint32_t v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void fence_sc_gpu() { asm volatile("fence.sc.gpu;" ::: "memory"); }
+
+// ---- children CSR -----------------------------------------------------------
+__global__ void edge_keys_kernel(const int32_t* __restrict__ nbr, int64_t rows, int k, int kp,
+                                 uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+  int64_t E = rows * k;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t r = e / k;
+    int a = (int)(e - r * k);
+    keys[e] = (uint32_t)nbr[r * kp + a];
+    vals[e] = (uint32_t)(r * kp + a);
+  }
+}
+
+__global__ void rowptr_kernel(const uint32_t* __restrict__ keys, int64_t E, int64_t N,
+                              int64_t* __restrict__ rowptr) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e <= E;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t prev = e == 0 ? -1 : (int64_t)keys[e - 1];
+    int64_t cur = e == E ? N : (int64_t)keys[e];
+    for (int64_t q = prev + 1; q <= cur; q++) rowptr[q] = e;
+  }
+}
+
+// Reverse sweep: chunk c may run once every chunk from the first chunk that
+// holds a child of its rows to the last one is complete.
+__global__ void chunk_need_rev_kernel(const int64_t* __restrict__ rowptr,
+                                      const int32_t* __restrict__ cedge, int kp, int64_t n0,
+                                      const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
+                                      int64_t n_chunks, int32_t* __restrict__ need) {
+  __shared__ int32_t smin[8];
+  int64_t c = blockIdx.x;
+  if (c >= n_chunks) return;
+  int32_t m = 0x7fffffff;
+  for (int32_t p = lo[c] + threadIdx.x; p < hi[c]; p += blockDim.x)
+    for (int64_t e = rowptr[p]; e < rowptr[p + 1]; e++)
+      m = min(m, (int32_t)(cedge[e] / kp + n0));
+  for (int o = 16; o; o >>= 1) m = min(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) smin[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); w++) m = min(m, smin[w]);
+    int32_t r = 0;
+    if (m != 0x7fffffff) {
+      int64_t a = 0, b = n_chunks - 1;
+      while (a < b) {
+        int64_t mid = (a + b + 1) / 2;
+        if (lo[mid] <= m) a = mid; else b = mid - 1;
+      }
+      r = (int32_t)(n_chunks - a);
+    }
+    need[c] = r;
+  }
+}
+
+// ---- dense helpers ------------------------------------------------------------
+// y_m = sum_{i >= m} M[i][m] x_i (transpose of a lower-triangular n0 x n0 M)
+__global__ void dense_lower_tmatvec_kernel(const float* __restrict__ M, const float* __restrict__ x,
+                                           float* __restrict__ y, int n0) {
+  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < n0; m += gridDim.x * blockDim.x) {
+    float s = 0.0f;
+    for (int i = m; i < n0; i++) s = fmaf(M[(int64_t)i * n0 + m], x[i], s);
+    y[m] = s;
+  }
+}
+
+// Lbar0[a][b] = sgn * u_a xi_b (b <= a) plus diag 2 logdetbar / L0_aa.
+__global__ void dense_lbar_kernel(const float* __restrict__ u, const float* __restrict__ xi,
+                                  const float* __restrict__ L0, int n0, float sgn, float ldbar,
+                                  float* __restrict__ out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)n0 * n0;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int a = (int)(e / n0), b = (int)(e % n0);
+    float v = 0.0f;
+    if (b <= a) v = sgn * u[a] * xi[b];
+    if (a == b) v += 2.0f * ldbar / L0[e];
+    out[e] = v;
+  }
+}
+
+// C = op(A) B for n x n row-major matrices; op(A) = A^T when transA.  If phi,
+// keeps the lower triangle of the result with the diagonal halved.
+__global__ void dense_gemm_kernel(const float* __restrict__ A, const float* __restrict__ B,
+                                  float* __restrict__ C, int n, int transA, int phi) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)n * n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int a = (int)(e / n), b = (int)(e % n);
+    if (phi && b > a) {
+      C[e] = 0.0f;
+      continue;
+    }
+    float s = 0.0f;
+    if (transA)
+      for (int m = 0; m < n; m++) s = fmaf(A[(int64_t)m * n + a], B[(int64_t)m * n + b], s);
+    else
+      for (int m = 0; m < n; m++) s = fmaf(A[(int64_t)a * n + m], B[(int64_t)m * n + b], s);
+    if (phi && a == b) s *= 0.5f;
+    C[e] = s;
+  }
+}
+
+__device__ void block_add3(double t0, double t1, double t2, double* out) {
+  __shared__ double red[3][32];
+  for (int o = 16; o; o >>= 1) {
+    t0 += __shfl_xor_sync(0xffffffffu, t0, o);
+    t1 += __shfl_xor_sync(0xffffffffu, t1, o);
+    t2 += __shfl_xor_sync(0xffffffffu, t2, o);
+  }
+  int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    red[0][w] = t0;
+    red[1][w] = t1;
+    red[2][w] = t2;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s0 = 0, s1 = 0, s2 = 0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); i++) {
+      s0 += red[0][i];
+      s1 += red[1][i];
+      s2 += red[2][i];
+    }
+    atomicAdd(out + 0, s0);
+    atomicAdd(out + 1, s1);
+    atomicAdd(out + 2, s2);
+  }
+}
+
+// theta_bar += sum_{a,b} Kbar[a][b] dK_ab/dtheta over the dense block.
+template <int KT>
+__global__ void dense_theta_kernel(const float* __restrict__ Kbar, const float4* __restrict__ xs,
+                                   int n0, KernF kf, double* __restrict__ thetabar) {
+  double tl = 0, ts = 0, tn = 0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)n0 * n0;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int a = (int)(e / n0), b = (int)(e % n0);
+    float kb = Kbar[e];
+    if (a == b) {
+      ts += kb;
+      tn += kb;
+    } else {
+      float d2 = sqdist(xs[a], xs[b]);
+      ts += (double)(kb * kappa_d2<KT>(kf, d2) / kf.s2);
+      tl += (double)(kb * dkappa_dell_d2<KT>(kf, d2));
+    }
+  }
+  block_add3(tl, ts, tn, thetabar);
+}
+
+// ---- whiten VJP: transposed gather ------------------------------------------------
+// vbar_p = base_p - sum over children (j, slot) of w_j b_j,slot, with
+// w_j = xibar_j / sigma_j; base_p = w_p for sparse p and (L0^-T xibar_0)_p
+// (already in vbar) for dense p.
+__global__ void whiten_transpose_kernel(const int64_t* __restrict__ rowptr,
+                                        const int32_t* __restrict__ cedge, int kp, int64_t n0,
+                                        const float* __restrict__ b, const float* __restrict__ sigma,
+                                        const float* __restrict__ xibar, float* __restrict__ vbar,
+                                        int64_t N) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < N;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    float acc = p < n0 ? vbar[p] : xibar[p] / sigma[p];
+    for (int64_t e = rowptr[p]; e < rowptr[p + 1]; e++) {
+      int32_t ce = cedge[e];
+      int64_t j = ce / kp + n0;
+      acc = fmaf(-(xibar[j] / sigma[j]), b[ce], acc);
+    }
+    vbar[p] = acc;
+  }
+}
+
+// ---- generate VJP: reverse level sweep (same scheme as the forward sweep,
+// chunks taken from the last one backwards) ----------------------------------------
+__global__ void __launch_bounds__(kSweepChunk) generate_adjoint_kernel(
+    const int64_t* __restrict__ rowptr, const int32_t* __restrict__ cedge, int kp, int64_t n0,
+    const float* __restrict__ b, const float* __restrict__ vbar, float* u,
+    const int32_t* __restrict__ chunk_lo, const int32_t* __restrict__ chunk_hi,
+    const int32_t* __restrict__ need_rev, int64_t n_chunks, uint32_t* sync, uint32_t* err,
+    int64_t max_spin) {
+  __shared__ int s_chunk;
+  __shared__ int s_abort;
+  uint32_t* ticket = sync;
+  uint32_t* water = sync + 1;  // trailing complete chunks
+  uint32_t* done = sync + 2;
+  const int tid = threadIdx.x;
+  while (true) {
+    if (tid == 0) s_chunk = (int)atomicAdd(ticket, 1u);
+    __syncthreads();
+    const int64_t t = s_chunk;
+    if (t >= n_chunks) break;
+    const int64_t c = n_chunks - 1 - t;
+    const int32_t lo = chunk_lo[c], hi = chunk_hi[c];
+    const uint32_t need = (uint32_t)need_rev[c];
+    const int64_t p = (int64_t)lo + tid;
+    const bool act = p < hi;
+    float acc = 0.0f;
+    int64_t e0 = 0, e1 = 0;
+    if (act) {
+      acc = vbar[p];
+      e0 = rowptr[p];
+      e1 = rowptr[p + 1];
+    }
+    if (tid == 0) {
+      int abort = 0;
+      if (ld_acq(water) < need) {
+        int64_t spins = 0;
+        while (ld_acq(water) < need) {
+          if (ld_acq(err) & ERRBIT_TIMEOUT) { abort = 1; break; }
+          if (++spins > max_spin) {
+            atomicOr(err, ERRBIT_TIMEOUT);
+            abort = 1;
+            break;
+          }
+          __nanosleep(64);
+        }
+      }
+      s_abort = abort;
+    }
+    __syncthreads();
+    if (s_abort) break;
+    for (int64_t e = e0; e < e1; e++) {
+      int32_t ce = cedge[e];
+      acc = fmaf(b[ce], __ldcg(u + (ce / kp + n0)), acc);
+    }
+    if (act) __stcg(u + p, acc);
+    __syncthreads();
+    if (tid == 0) {
+      fence_sc_gpu();
+      st_rel(done + c, 1u);
+      fence_sc_gpu();
+      uint32_t w = ld_acq(water), w0 = w;
+      while (w < (uint32_t)n_chunks && ld_acq(done + (n_chunks - 1 - w))) w++;
+      if (w > w0) atomicMax(water, w);
+    }
+  }
+}
+
+// u for the dense positions, whose children are all sparse rows.
+__global__ void dense_children_kernel(const int64_t* __restrict__ rowptr,
+                                      const int32_t* __restrict__ cedge, int kp, int64_t n0,
+                                      const float* __restrict__ b, const float* __restrict__ vbar,
+                                      float* __restrict__ u) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n0;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    float acc = vbar[p];
+    for (int64_t e = rowptr[p]; e < rowptr[p + 1]; e++) {
+      int32_t ce = cedge[e];
+      acc = fmaf(b[ce], u[ce / kp + n0], acc);
+    }
+    u[p] = acc;
+  }
+}
+
+// ---- per-row factor backward ------------------------------------------------------
+// mode 0 (whiten): alpha_i = -xibar_i / sigma_i, beta = 2 logdetbar.
+// mode 1 (generate): alpha_i = u_i, beta = 0; also writes xibar_i = sigma_i u_i.
+// bbar_i = alpha_i v_c(i), sigbar_i = alpha_i xi_i + beta / sigma_i.
+template <int G, int KT>
+__global__ void __launch_bounds__(128) factor_backward_kernel(
+    const float4* __restrict__ xs, const int32_t* __restrict__ nbr, int64_t N, int k, int kp,
+    int64_t n0, KernF kf, int mode, const float* __restrict__ coef, float beta,
+    const float* __restrict__ v, const float* __restrict__ xi, float* __restrict__ xibar_out,
+    double* __restrict__ thetabar) {
+  constexpr int PPW = 32 / G;
+  constexpr int GS = PFLayout<G>::GS;
+  __shared__ __align__(16) float Ls[4 * PPW * GS];
+  const int lane = threadIdx.x & 31;
+  const int grp = lane / G;
+  const int a = lane % G;
+  const int warp = threadIdx.x >> 5;
+  const unsigned full = 0xffffffffu;
+  float* Lg = Ls + (warp * PPW + grp) * GS;
+  double tl = 0.0, ts = 0.0, tn = 0.0;
+  const int64_t total_groups = (int64_t)gridDim.x * 4 * PPW;
+  const int64_t gid = ((int64_t)blockIdx.x * 4 + warp) * PPW + grp;
+  const int64_t npts = N - n0;
+  const int64_t iters = (npts + total_groups - 1) / total_groups;
+  const float inv_s2 = 1.0f / kf.s2;
+  for (int64_t it = 0; it < iters; it++) {
+    int64_t t = it * total_groups + gid;
+    bool valid = t < npts;
+    int64_t i = n0 + (valid ? t : 0);
+    bool real = a < k;
+    int32_t ca = real ? nbr[(i - n0) * kp + a] : 0;
+    PointState<G> st;
+    point_factor_group<G, KT>(st, a, k, kf, xs[ca], xs[i], Lg);
+    __syncwarp();
+    float sigma = st.sigma;
+    float ci = coef[i];
+    float alpha = mode == 0 ? -ci / sigma : ci;
+    float xii = xi[i];
+    float sigbar = alpha * xii + beta / sigma;
+    float sbar = sigbar / (2.0f * sigma);
+    float bbar = real ? alpha * v[ca] : 0.0f;
+    float g = group_chol_solve<G>(st, a, k, bbar, Lg);
+    __syncwarp();
+    // row a of Kbar against dK/dtheta
+    float pl = 0.0f, ps = 0.0f, pn = 0.0f;
+    float ba = st.b_own;
+#pragma unroll
+    for (int c = 0; c < G; c++) {
+      if (c >= k) break;
+      float bc = __shfl_sync(full, st.b_own, c, G);
+      float kb = -g * bc + sbar * ba * bc;
+      if (c == a) {
+        ps += kb;
+        pn += kb;
+      } else {
+        float d2 = st.D2[c];
+        ps += kb * kappa_d2<KT>(kf, d2) * inv_s2;
+        pl += kb * dkappa_dell_d2<KT>(kf, d2);
+      }
+    }
+    {
+      float kci = g - 2.0f * sbar * ba;
+      ps += kci * kappa_d2<KT>(kf, st.d2q) * inv_s2;
+      pl += kci * dkappa_dell_d2<KT>(kf, st.d2q);
+    }
+    if (!real) pl = ps = pn = 0.0f;
+    if (a == 0) {  // Kbar_ii = sbar
+      ps += sbar;
+      pn += sbar;
+    }
+#pragma unroll
+    for (int o = G / 2; o; o >>= 1) {
+      pl += __shfl_xor_sync(full, pl, o, G);
+      ps += __shfl_xor_sync(full, ps, o, G);
+      pn += __shfl_xor_sync(full, pn, o, G);
+    }
+    if (valid && a == 0) {
+      tl += pl;
+      ts += ps;
+      tn += pn;
+      if (mode == 1) xibar_out[i] = sigma * ci;
+    }
+  }
+  block_add3(tl, ts, tn, thetabar);
+}
+
+__global__ void scale_kernel(const float* __restrict__ x, float s, float* __restrict__ y,
+                             int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = s * x[i];
+}
+
+template <int G>
+int launch_factor_backward(graphgp_graph_t g, graphgp_factor_t f, int mode, const float* coef,
+                           float beta, const float* v, const float* xi, float* xibar,
+                           double* thetabar, cudaStream_t s) {
+  int64_t npts = g->N - g->n0;
+  if (npts <= 0) return GRAPHGP_OK;
+  constexpr int PPW = 32 / G;
+  unsigned grid = grid_for((npts + 4 * PPW - 1) / (4 * PPW) * 128, 128, 16);
+  KernF kf = make_kernf(f->kern);
+#define GGP_FB(KT)                                                                          \
+  factor_backward_kernel<G, KT><<<grid, 128, 0, s>>>(g->xs, g->nbr, g->N, g->k, g->kp, g->n0, \
+                                                     kf, mode, coef, beta, v, xi, xibar,     \
+                                                     thetabar)
+  switch (f->kern.type) {
+    case GRAPHGP_MATERN12: GGP_FB(GRAPHGP_MATERN12); break;
+    case GRAPHGP_MATERN32: GGP_FB(GRAPHGP_MATERN32); break;
+    case GRAPHGP_MATERN52: GGP_FB(GRAPHGP_MATERN52); break;
+    default: GGP_FB(GRAPHGP_SQEXP); break;
+  }
+#undef GGP_FB
+  GGP_CUDA(cudaGetLastError());
+  return GRAPHGP_OK;
+}
+
+int factor_backward(graphgp_graph_t g, graphgp_factor_t f, int mode, const float* coef,
+                    float beta, const float* v, const float* xi, float* xibar, double* thetabar,
+                    cudaStream_t s) {
+  if (g->k <= 8) return launch_factor_backward<8>(g, f, mode, coef, beta, v, xi, xibar, thetabar, s);
+  if (g->k <= 16) return launch_factor_backward<16>(g, f, mode, coef, beta, v, xi, xibar, thetabar, s);
+  return launch_factor_backward<32>(g, f, mode, coef, beta, v, xi, xibar, thetabar, s);
+}
+
+// Dense block backward from Lbar0 (built from u, xi_0 by dense_lbar_kernel).
+int dense_backward(graphgp_graph_t g, graphgp_factor_t f, const float* u0, const float* xi0,
+                   float sgn, float ldbar, double* thetabar, cudaStream_t s) {
+  int n0 = g->n0;
+  int64_t nn = (int64_t)n0 * n0;
+  Scratch sc(s);
+  float *Lb = nullptr, *P = nullptr, *T = nullptr;
+  GGP_TRY(sc.alloc(&Lb, nn));
+  GGP_TRY(sc.alloc(&P, nn));
+  GGP_TRY(sc.alloc(&T, nn));
+  unsigned grid = grid_for(nn, 256);
+  dense_lbar_kernel<<<grid, 256, 0, s>>>(u0, xi0, f->L0, n0, sgn, ldbar, Lb);
+  dense_gemm_kernel<<<grid, 256, 0, s>>>(f->L0, Lb, P, n0, 1, 1);      // Phi(L0^T Lbar0)
+  dense_gemm_kernel<<<grid, 256, 0, s>>>(f->L0inv, P, T, n0, 1, 0);    // L0^-T P
+  dense_gemm_kernel<<<grid, 256, 0, s>>>(T, f->L0inv, Lb, n0, 0, 0);   // (L0^-T P) L0^-1
+  KernF kf = make_kernf(f->kern);
+  switch (f->kern.type) {
+    case GRAPHGP_MATERN12: dense_theta_kernel<GRAPHGP_MATERN12><<<grid, 256, 0, s>>>(Lb, g->xs, n0, kf, thetabar); break;
+    case GRAPHGP_MATERN32: dense_theta_kernel<GRAPHGP_MATERN32><<<grid, 256, 0, s>>>(Lb, g->xs, n0, kf, thetabar); break;
+    case GRAPHGP_MATERN52: dense_theta_kernel<GRAPHGP_MATERN52><<<grid, 256, 0, s>>>(Lb, g->xs, n0, kf, thetabar); break;
+    default: dense_theta_kernel<GRAPHGP_SQEXP><<<grid, 256, 0, s>>>(Lb, g->xs, n0, kf, thetabar); break;
+  }
+  GGP_CUDA(cudaGetLastError());
+  return GRAPHGP_OK;
+}
+
+}  // namespace
+
+int build_child_csr(graphgp_graph_t g, cudaStream_t s) {
+  if (g->csr.rowptr) return GRAPHGP_OK;
+  int64_t rows = g->N - g->n0;
+  int64_t E = rows * g->k;
+  if (rows * g->kp >= ((int64_t)1 << 31)) return GRAPHGP_ERR_INVALID;
+  ChildCSR c;
+  GGP_TRY(g->mem.alloc(&c.rowptr, g->N + 1));
+  GGP_TRY(g->mem.alloc(&c.child, E));
+  GGP_TRY(g->mem.alloc(&c.need_rev, g->n_chunks));
+  c.edges = E;
+  Scratch sc(s);
+  if (E > 0) {
+    uint32_t *keys = nullptr, *vals = nullptr, *ks = nullptr;
+    GGP_TRY(sc.alloc(&keys, E));
+    GGP_TRY(sc.alloc(&vals, E));
+    GGP_TRY(sc.alloc(&ks, E));
+    edge_keys_kernel<<<grid_for(E, 256), 256, 0, s>>>(g->nbr, rows, g->k, g->kp, keys, vals);
+    GGP_CUDA(cudaGetLastError());
+    int bits = 0;
+    while (((int64_t)1 << bits) < g->N) bits++;
+    GGP_TRY(radix_sort_pairs(keys, vals, ks, (uint32_t*)c.child, E, bits, s));
+    rowptr_kernel<<<grid_for(E + 1, 256), 256, 0, s>>>(ks, E, g->N, c.rowptr);
+    GGP_CUDA(cudaGetLastError());
+  } else {
+    GGP_CUDA(cudaMemsetAsync(c.rowptr, 0, (g->N + 1) * sizeof(int64_t), s));
+  }
+  if (g->n_chunks) {
+    chunk_need_rev_kernel<<<(unsigned)g->n_chunks, 256, 0, s>>>(c.rowptr, c.child, g->kp, g->n0,
+                                                                g->chunk_lo, g->chunk_hi,
+                                                                g->n_chunks, c.need_rev);
+    GGP_CUDA(cudaGetLastError());
+  }
+  GGP_CUDA(cudaStreamSynchronize(s));
+  g->csr = c;
+  return GRAPHGP_OK;
+}
+
+int run_whiten_backward(graphgp_graph_t g, graphgp_factor_t f, const float* v, const float* xi,
+                        const float* xibar, double logdetbar, float* vbar, double* thetabar,
+                        cudaStream_t s) {
+  GGP_TRY(build_child_csr(g, s));
+  int n0 = g->n0;
+  // dense: vbar_0 = L0^-T xibar_0 (then children are subtracted below)
+  dense_lower_tmatvec_kernel<<<(n0 + 255) / 256, 256, 0, s>>>(f->L0inv, xibar, vbar, n0);
+  GGP_CUDA(cudaGetLastError());
+  GGP_TRY(dense_backward(g, f, vbar, xi, -1.0f, (float)logdetbar, thetabar, s));
+  whiten_transpose_kernel<<<grid_for(g->N, 256), 256, 0, s>>>(g->csr.rowptr, g->csr.child, g->kp,
+                                                              n0, f->b, f->sigma, xibar, vbar,
+                                                              g->N);
+  GGP_CUDA(cudaGetLastError());
+  GGP_TRY(factor_backward(g, f, 0, xibar, (float)(2.0 * logdetbar), v, xi, nullptr, thetabar, s));
+  return GRAPHGP_OK;
+}
+
+int run_generate_backward(graphgp_graph_t g, graphgp_factor_t f, const float* xi, const float* v,
+                          const float* vbar, float* xibar, double* thetabar, cudaStream_t s) {
+  GGP_TRY(build_child_csr(g, s));
+  float* u = g->tmp_vec;
+  int n0 = g->n0;
+  if (g->n_chunks) {
+    GGP_CUDA(cudaMemsetAsync(g->sweep_sync, 0, (2 + g->n_chunks) * sizeof(uint32_t), s));
+    static int bps = 0;
+    if (!bps) {
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, generate_adjoint_kernel, kSweepChunk, 0);
+      if (bps < 1) bps = 1;
+    }
+    int64_t grid = std::min<int64_t>((int64_t)num_sms() * bps, g->n_chunks);
+    generate_adjoint_kernel<<<(unsigned)grid, kSweepChunk, 0, s>>>(
+        g->csr.rowptr, g->csr.child, g->kp, n0, f->b, vbar, u, g->chunk_lo, g->chunk_hi,
+        g->csr.need_rev, g->n_chunks, g->sweep_sync, g->err, g->max_spin);
+    GGP_CUDA(cudaGetLastError());
+  }
+  dense_children_kernel<<<(n0 + 255) / 256, 256, 0, s>>>(g->csr.rowptr, g->csr.child, g->kp, n0,
+                                                         f->b, vbar, u);
+  GGP_CUDA(cudaGetLastError());
+  // dense: xibar_0 = L0^T u_0, Lbar0 = tril(u_0 xi_0^T)
+  dense_lower_tmatvec_kernel<<<(n0 + 255) / 256, 256, 0, s>>>(f->L0, u, xibar, n0);
+  GGP_CUDA(cudaGetLastError());
+  GGP_TRY(dense_backward(g, f, u, xi, 1.0f, 0.0f, thetabar, s));
+  GGP_TRY(factor_backward(g, f, 1, u, 0.0f, v, xi, xibar, thetabar, s));
+  return GRAPHGP_OK;
+}
+
+int run_whiten(graphgp_graph_t g, graphgp_factor_t f, const float* v, float* xi, double* sq,
+               cudaStream_t s);
+
+}  // namespace ggp
+
+using namespace ggp;
+
+static bool pair_ok(graphgp_graph_t g, graphgp_factor_t f) { return g && f && f->g == g; }
+
+extern "C" int graphgp_generate_backward(graphgp_graph_t g, graphgp_factor_t f, const float* xi_d,
+                                         const float* v_d, const float* vbar_d, float* xibar_d,
+                                         double* thetabar_d, void* stream) {
+  if (!pair_ok(g, f) || !xi_d || !v_d || !vbar_d || !xibar_d || !thetabar_d)
+    return GRAPHGP_ERR_INVALID;
+  return run_generate_backward(g, f, xi_d, v_d, vbar_d, xibar_d, thetabar_d, (cudaStream_t)stream);
+}
+
+extern "C" int graphgp_whiten_backward(graphgp_graph_t g, graphgp_factor_t f, const float* v_d,
+                                       const float* xi_d, const float* xibar_d, double logdetbar,
+                                       float* vbar_d, double* thetabar_d, void* stream) {
+  if (!pair_ok(g, f) || !xi_d || !v_d || !xibar_d || !vbar_d || !thetabar_d)
+    return GRAPHGP_ERR_INVALID;
+  return run_whiten_backward(g, f, v_d, xi_d, xibar_d, logdetbar, vbar_d, thetabar_d,
+                             (cudaStream_t)stream);
+}
+
+extern "C" int graphgp_nll_backward(graphgp_graph_t g, graphgp_factor_t f, const float* v_d,
+                                    double nllbar, float* vbar_d, double* thetabar_d,
+                                    void* stream) {
+  if (!pair_ok(g, f) || !v_d || !vbar_d || !thetabar_d) return GRAPHGP_ERR_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  float* xi = g->tmp_vec2;
+  float* xibar = g->tmp_vec;
+  GGP_TRY(run_whiten(g, f, v_d, xi, nullptr, s));
+  scale_kernel<<<grid_for(g->N, 256), 256, 0, s>>>(xi, (float)nllbar, xibar, g->N);
+  GGP_CUDA(cudaGetLastError());
+  return run_whiten_backward(g, f, v_d, xi, xibar, 0.5 * nllbar, vbar_d, thetabar_d, s);
+}

@@ -1,0 +1,271 @@
+// Internal definitions shared by the CUDA translation units of libgraphgp.
+// GraphGP: "GraphGP: Scalable Gaussian Processes with Vecchia's Approximation".
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+#include <vector>
+
+#include "graphgp.h"
+
+namespace ggp {
+
+// ---------------------------------------------------------------------------
+// error plumbing
+// ---------------------------------------------------------------------------
+struct Status {
+  int code = GRAPHGP_OK;
+};
+
+#define GGP_CUDA(call)                                                    \
+  do {                                                                    \
+    cudaError_t e_ = (call);                                              \
+    if (e_ != cudaSuccess) {                                              \
+      std::fprintf(stderr, "graphgp: %s failed: %s (%s:%d)\n", #call,     \
+                   cudaGetErrorString(e_), __FILE__, __LINE__);           \
+      return (e_ == cudaErrorMemoryAllocation) ? GRAPHGP_ERR_OOM          \
+                                               : GRAPHGP_ERR_CUDA;        \
+    }                                                                     \
+  } while (0)
+
+#define GGP_TRY(expr)           \
+  do {                          \
+    int rc_ = (expr);           \
+    if (rc_ < 0) return rc_;    \
+  } while (0)
+
+// bits of the device error word held by every graph
+enum : uint32_t { ERRBIT_TIMEOUT = 1u, ERRBIT_INDEX = 2u };
+
+// Device allocation that remembers its size (for graphgp_graph_info).
+struct DevArena {
+  std::vector<void*> ptrs;
+  size_t bytes = 0;
+  template <class T>
+  int alloc(T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    size_t b = count * sizeof(T);
+    cudaError_t e = cudaMalloc((void**)p, b);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      *p = nullptr;
+      return e == cudaErrorMemoryAllocation ? GRAPHGP_ERR_OOM : GRAPHGP_ERR_CUDA;
+    }
+    ptrs.push_back((void*)*p);
+    bytes += b;
+    return GRAPHGP_OK;
+  }
+  void release(void* p, size_t b) {
+    for (auto& q : ptrs)
+      if (q == p) {
+        cudaFree(q);
+        q = nullptr;
+        bytes -= b;
+      }
+  }
+  void free_all() {
+    for (void* p : ptrs)
+      if (p) cudaFree(p);
+    ptrs.clear();
+    bytes = 0;
+  }
+};
+
+// Stream-ordered scratch that lives for one host call: allocated and freed
+// on the call's stream, so it is released only after the work that uses it.
+struct Scratch {
+  cudaStream_t s;
+  std::vector<void*> ptrs;
+  explicit Scratch(cudaStream_t st) : s(st) {}
+  template <class T>
+  int alloc(T** p, size_t count) {
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMallocAsync((void**)p, count * sizeof(T), s);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      *p = nullptr;
+      return e == cudaErrorMemoryAllocation ? GRAPHGP_ERR_OOM : GRAPHGP_ERR_CUDA;
+    }
+    ptrs.push_back((void*)*p);
+    return GRAPHGP_OK;
+  }
+  ~Scratch() {
+    for (void* p : ptrs) cudaFreeAsync(p, s);
+  }
+};
+
+// Rows of the neighbour and weight matrices are padded to a multiple of four
+// entries so that every row starts on a 16-byte boundary; padding entries
+// point at position 0 with weight 0.
+inline int row_stride(int k) { return (k + 3) & ~3; }
+
+// Points per chunk of the level sweeps; chunks never straddle a depth level.
+constexpr int kSweepChunk = 256;
+
+// Children (transposed graph) in CSR form, built on first use by the
+// adjoint sweeps.
+struct ChildCSR {
+  int64_t* rowptr = nullptr;    // [N+1]
+  int32_t* child = nullptr;     // [E] entry (row * kp + slot) of the child's row
+  int32_t* need_rev = nullptr;  // [n_chunks] trailing chunks a chunk waits for
+  int64_t edges = 0;
+};
+
+}  // namespace ggp
+
+// The handle types named in graphgp.h.
+struct graphgp_graph_s {
+  int64_t N = 0;
+  int k = 0, kp = 0, n0 = 0, num_levels = 0;
+  int64_t max_spin = 0;
+  ggp::DevArena mem;
+  float* pts_in = nullptr;     // [N*3] input order, canonicalised
+  float4* xs = nullptr;        // [N] coordinates in graph order (w unused)
+  int32_t* order = nullptr;    // [N] position -> input index
+  int32_t* nbr = nullptr;      // [(N-n0)*kp] positions, nearest first
+  std::vector<int64_t> level_off_h;  // [num_levels+1]
+  int64_t* level_off_d = nullptr;
+  // sweep chunks (levels >= 1)
+  int64_t n_chunks = 0;
+  int32_t* chunk_lo = nullptr;    // [n_chunks]
+  int32_t* chunk_hi = nullptr;    // [n_chunks]
+  int32_t* chunk_need = nullptr;  // [n_chunks] chunks that must be complete
+  int32_t* chunk_level = nullptr; // [n_chunks]
+  uint32_t* sweep_sync = nullptr; // [2 + n_chunks]: ticket, watermark, done
+  uint32_t* err = nullptr;        // device error word
+  // tree (graphs built here only)
+  bool has_tree = false;
+  int32_t* tree_point = nullptr;
+  uint8_t* split_dim = nullptr;
+  int32_t* inorder = nullptr;
+  int32_t* depth_tree = nullptr;
+  int32_t* nbr_tree = nullptr;   // [(N-n0)*k]
+  // transposed graph for adjoints (lazy)
+  ggp::ChildCSR csr;
+  float* tmp_vec = nullptr;      // [N] work vector for nll / adjoints
+  float* tmp_vec2 = nullptr;     // [N]
+};
+
+struct graphgp_factor_s {
+  graphgp_graph_t g = nullptr;
+  graphgp_kernel kern{};
+  ggp::DevArena mem;
+  float* b = nullptr;        // [(N-n0)*kp]
+  float* sigma = nullptr;    // [N]
+  float* L0 = nullptr;       // [n0*n0] row-major lower
+  float* L0inv = nullptr;    // [n0*n0] row-major lower
+  double* logdet = nullptr;  // [1]
+  unsigned long long* not_pd = nullptr;  // [1]
+};
+
+namespace ggp {
+
+// ---------------------------------------------------------------------------
+// FP32 covariance (Sec. 2.1): kappa from the squared distance.
+// ---------------------------------------------------------------------------
+struct KernF {
+  float s2, inv_ell, nug;
+};
+
+template <int KT>
+__device__ __forceinline__ float kappa_d2(const KernF& p, float d2) {
+  if (KT == GRAPHGP_SQEXP) {
+    return p.s2 * expf(-0.5f * d2 * p.inv_ell * p.inv_ell);
+  } else {
+    float r = sqrtf(d2);
+    if (KT == GRAPHGP_MATERN12) {
+      return p.s2 * expf(-r * p.inv_ell);
+    } else if (KT == GRAPHGP_MATERN32) {
+      float a = 1.7320508075688772f * r * p.inv_ell;
+      return p.s2 * (1.0f + a) * expf(-a);
+    } else {
+      float a = 2.2360679774997896f * r * p.inv_ell;
+      return p.s2 * (1.0f + a + a * a * (1.0f / 3.0f)) * expf(-a);
+    }
+  }
+}
+
+// d kappa / d lengthscale from the squared distance (FP32).
+template <int KT>
+__device__ __forceinline__ float dkappa_dell_d2(const KernF& p, float d2) {
+  float il = p.inv_ell;
+  if (KT == GRAPHGP_SQEXP) {
+    return p.s2 * expf(-0.5f * d2 * il * il) * d2 * il * il * il;
+  } else {
+    float r = sqrtf(d2);
+    if (KT == GRAPHGP_MATERN12) {
+      return p.s2 * expf(-r * il) * r * il * il;
+    } else if (KT == GRAPHGP_MATERN32) {
+      float a = 1.7320508075688772f * r * il;
+      return p.s2 * a * a * expf(-a) * il;
+    } else {
+      float a = 2.2360679774997896f * r * il;
+      return p.s2 * a * a * (1.0f + a) * expf(-a) * il * (1.0f / 3.0f);
+    }
+  }
+}
+
+__device__ __forceinline__ float sqdist(float4 a, float4 b) {
+  float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
+  return fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+}
+
+inline KernF make_kernf(const graphgp_kernel& k) {
+  KernF p;
+  p.s2 = (float)k.sigma2;
+  p.inv_ell = (float)(1.0 / k.lengthscale);
+  p.nug = (float)k.nugget;
+  return p;
+}
+
+inline int num_sms() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+inline unsigned grid_for(int64_t n, int block, int64_t cap_per_sm = 32) {
+  int64_t g = (n + block - 1) / block;
+  int64_t cap = (int64_t)num_sms() * cap_per_sm;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (unsigned)g;
+}
+
+// ---------------------------------------------------------------------------
+// entry points implemented across translation units
+// ---------------------------------------------------------------------------
+// radix sort of (key, value) pairs, stable, keys compared on `bits` low bits
+int radix_sort_pairs(const uint32_t* keys_in, const uint32_t* vals_in,
+                     uint32_t* keys_out, uint32_t* vals_out, int64_t n,
+                     int bits, cudaStream_t s);
+// exclusive scan of uint32 counts into uint32 offsets; returns total on request
+int scan_exclusive_u32(const uint32_t* in, uint32_t* out, int64_t n,
+                       cudaStream_t s);
+
+int tree_build(const float* pts, int64_t N, int rule, int32_t* tree_point,
+               uint8_t* split_dim, int32_t* inorder, int32_t* node_at_inorder,
+               cudaStream_t s);
+int knn_query(const float* pts, const int32_t* tree_point,
+              const uint8_t* split_dim, const int32_t* node_at_inorder,
+              int64_t N, int k, int64_t n0, int32_t* nbr_tree, uint32_t* err,
+              cudaStream_t s);
+
+int graph_finish_device(graphgp_graph_t g, cudaStream_t s);  // chunks + sync
+
+int dense_factor(graphgp_graph_t g, graphgp_factor_t f, const KernF& kp,
+                 int type, cudaStream_t s);
+int point_factor(graphgp_graph_t g, graphgp_factor_t f, const KernF& kp,
+                 int type, cudaStream_t s);
+
+int build_child_csr(graphgp_graph_t g, cudaStream_t s);
+
+}  // namespace ggp

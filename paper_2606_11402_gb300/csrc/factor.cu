@@ -1,0 +1,279 @@
+// Per-point conditioning factors (Sec. 2.1 Eq. 2; Alg. 1) and the dense
+// initial block (Alg. 1, first line; Sec. 2.2 "Batch construction").
+//
+// Per point i with c = c(i): b_i = K_ic K_cc^-1 and sigma_i^2 =
+// K_ii - K_ic K_cc^-1 K_ci.  A group of G lanes (G = 8, 16 or 32 >= k) of one
+// warp owns one point; lane a holds row a of K_cc in registers.  The
+// Cholesky factor is built column by column (left-looking): at step j every
+// lane forms its Schur value from its own row and row j of L, which lane j
+// published to shared memory in earlier steps; lane j's value is the pivot.
+// The forward solve y = L^-1 K_ci rides along (right-looking on the lanes'
+// K_ci entries), sigma^2 = K_ii - y.y is accumulated in compensated FP32
+// (two-sum / two-product), and b = L^-T y is a backward sweep reading L's
+// columns from shared memory.  Pivots below 1e-7 of their diagonal entry are
+// raised to that floor and counted.  logdet = sum log sigma_i^2 is reduced in
+// FP64 from the stored FP32 sigma (a running FP64 product with separate
+// exponent, one log per thread).
+#include "pointfactor.cuh"
+
+namespace ggp {
+namespace {
+
+// Running product of sigma^2 values in FP64 with a separate binary exponent.
+struct LogAcc {
+  double m = 1.0;
+  int e = 0;
+  __device__ void mul(float sigma) {
+    m *= (double)sigma * (double)sigma;
+    int ex;
+    m = frexp(m, &ex);
+    e += ex;
+  }
+  __device__ double log_value() const { return log(m) + (double)e * 0.69314718055994530942; }
+};
+
+__device__ void block_add_double(double v, double* out) {
+  __shared__ double red[32];
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) red[w] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); i++) s += red[i];
+    atomicAdd(out, s);
+  }
+}
+
+template <int G, int KT>
+__global__ void __launch_bounds__(128) point_factor_kernel(
+    const float4* __restrict__ xs, const int32_t* __restrict__ nbr, int64_t N, int k, int kp,
+    int64_t n0, KernF kf, float* __restrict__ b_out, float* __restrict__ sigma_out,
+    double* __restrict__ logdet, unsigned long long* __restrict__ not_pd) {
+  constexpr int PPW = 32 / G;  // points per warp
+  constexpr int GS = PFLayout<G>::GS;
+  __shared__ __align__(16) float Ls[4 * PPW * GS];
+  const int lane = threadIdx.x & 31;
+  const int grp = lane / G;
+  const int a = lane % G;
+  const int warp = threadIdx.x >> 5;
+  float* Lg = Ls + (warp * PPW + grp) * GS;
+  LogAcc acc;
+  unsigned long long clamped_rows = 0;
+  const int64_t total_groups = (int64_t)gridDim.x * 4 * PPW;
+  const int64_t gid = ((int64_t)blockIdx.x * 4 + warp) * PPW + grp;
+  const int64_t npts = N - n0;
+  const int64_t iters = (npts + total_groups - 1) / total_groups;
+  for (int64_t it = 0; it < iters; it++) {
+    int64_t t = it * total_groups + gid;
+    bool valid = t < npts;
+    int64_t i = n0 + (valid ? t : 0);
+    int32_t ca = a < k ? nbr[(i - n0) * kp + a] : 0;
+    PointState<G> st;
+    point_factor_group<G, KT>(st, a, k, kf, xs[ca], xs[i], Lg);
+    __syncwarp();
+    if (valid) {
+      if (a < kp) b_out[(i - n0) * kp + a] = a < k ? st.b_own : 0.0f;
+      if (a == 0) {
+        sigma_out[i] = st.sigma;
+        acc.mul(st.sigma);
+        if (st.clamped) clamped_rows++;
+      }
+    }
+  }
+  double lv = (a == 0) ? acc.log_value() : 0.0;
+  block_add_double(lv, logdet);
+  for (int o = 16; o; o >>= 1) clamped_rows += __shfl_xor_sync(0xffffffffu, clamped_rows, o);
+  if (lane == 0 && clamped_rows) atomicAdd(not_pd, clamped_rows);
+}
+
+// Dense block: K_00 (lower triangle) in global memory.
+template <int KT>
+__global__ void dense_fill_kernel(const float4* __restrict__ xs, int n0, KernF kf,
+                                  float* __restrict__ A) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)n0 * n0;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int i = (int)(e / n0), j = (int)(e % n0);
+    float v = 0.0f;
+    if (j < i) v = kappa_d2<KT>(kf, sqdist(xs[i], xs[j]));
+    else if (j == i) v = kf.s2 + kf.nug;
+    A[e] = v;
+  }
+}
+
+// One block, left-looking Cholesky by columns on the n0 x n0 matrix in
+// global memory (L2-resident), with the pivot floor; then L0^-1 column by
+// column; sigma_i = L0_ii; adds sum log L0_ii^2 to logdet.
+__global__ void __launch_bounds__(1024) dense_chol_kernel(float* __restrict__ A,
+                                                          float* __restrict__ W, int n0,
+                                                          float* __restrict__ sigma,
+                                                          double* __restrict__ logdet,
+                                                          unsigned long long* __restrict__ not_pd) {
+  extern __shared__ float rowj[];  // [n0]
+  __shared__ float s_inv;
+  __shared__ unsigned long long s_bad;
+  if (threadIdx.x == 0) s_bad = 0;
+  const float k0 = A[0];
+  for (int j = 0; j < n0; j++) {
+    for (int m = threadIdx.x; m < j; m += blockDim.x) rowj[m] = A[(int64_t)j * n0 + m];
+    __syncthreads();
+    for (int r = j + threadIdx.x; r < n0; r += blockDim.x) {
+      const float* ar = A + (int64_t)r * n0;
+      float t0 = ar[j], t1 = 0.0f;
+      int m = 0;
+      for (; m + 1 < j; m += 2) {
+        t0 = fmaf(-ar[m], rowj[m], t0);
+        t1 = fmaf(-ar[m + 1], rowj[m + 1], t1);
+      }
+      if (m < j) t0 = fmaf(-ar[m], rowj[m], t0);
+      float tv = t0 + t1;
+      if (r == j) {
+        float fl = kPdFloor * k0;
+        if (!(tv > fl)) {
+          tv = fl;
+          s_bad++;
+        }
+        float l = sqrtf(tv);
+        A[(int64_t)j * n0 + j] = l;
+        s_inv = 1.0f / l;
+      } else {
+        rowj[n0 - 1 - (r - j - 1)] = tv;  // park in the unused tail of rowj
+      }
+    }
+    __syncthreads();
+    float inv = s_inv;
+    for (int r = j + 1 + threadIdx.x; r < n0; r += blockDim.x)
+      A[(int64_t)r * n0 + j] = rowj[n0 - 1 - (r - j - 1)] * inv;
+    __syncthreads();
+  }
+  // inverse: column c solves L w = e_c
+  for (int c = threadIdx.x; c < n0; c += blockDim.x) {
+    for (int i = 0; i < c; i++) W[(int64_t)i * n0 + c] = 0.0f;
+    W[(int64_t)c * n0 + c] = 1.0f / A[(int64_t)c * n0 + c];
+    for (int i = c + 1; i < n0; i++) {
+      const float* ar = A + (int64_t)i * n0;
+      float t = 0.0f;
+      for (int m = c; m < i; m++) t = fmaf(ar[m], W[(int64_t)m * n0 + c], t);
+      W[(int64_t)i * n0 + c] = -t / ar[i];
+    }
+  }
+  __syncthreads();
+  double lsum = 0.0;
+  for (int i = threadIdx.x; i < n0; i += blockDim.x) {
+    float l = A[(int64_t)i * n0 + i];
+    sigma[i] = l;
+    lsum += log((double)l * (double)l);
+  }
+  block_add_double(lsum, logdet);
+  if (threadIdx.x == 0 && s_bad) atomicAdd(not_pd, s_bad);
+}
+
+template <int G>
+int launch_point(int type, graphgp_graph_t g, graphgp_factor_t f, const KernF& kf,
+                 cudaStream_t s) {
+  int64_t npts = g->N - g->n0;
+  constexpr int PPW = 32 / G;
+  int64_t groups_per_block = 4 * PPW;
+  unsigned grid = grid_for((npts + groups_per_block - 1) / groups_per_block * 128, 128, 16);
+#define GGP_PF(KT)                                                                       \
+  point_factor_kernel<G, KT><<<grid, 128, 0, s>>>(g->xs, g->nbr, g->N, g->k, g->kp, g->n0, \
+                                                  kf, f->b, f->sigma, f->logdet, f->not_pd)
+  switch (type) {
+    case GRAPHGP_MATERN12: GGP_PF(GRAPHGP_MATERN12); break;
+    case GRAPHGP_MATERN32: GGP_PF(GRAPHGP_MATERN32); break;
+    case GRAPHGP_MATERN52: GGP_PF(GRAPHGP_MATERN52); break;
+    default: GGP_PF(GRAPHGP_SQEXP); break;
+  }
+#undef GGP_PF
+  GGP_CUDA(cudaGetLastError());
+  return GRAPHGP_OK;
+}
+
+}  // namespace
+
+int point_factor(graphgp_graph_t g, graphgp_factor_t f, const KernF& kf, int type,
+                 cudaStream_t s) {
+  if (g->N <= g->n0) return GRAPHGP_OK;
+  if (g->k <= 8) return launch_point<8>(type, g, f, kf, s);
+  if (g->k <= 16) return launch_point<16>(type, g, f, kf, s);
+  return launch_point<32>(type, g, f, kf, s);
+}
+
+int dense_factor(graphgp_graph_t g, graphgp_factor_t f, const KernF& kf, int type,
+                 cudaStream_t s) {
+  int n0 = g->n0;
+  unsigned grid = grid_for((int64_t)n0 * n0, 256);
+  switch (type) {
+    case GRAPHGP_MATERN12: dense_fill_kernel<GRAPHGP_MATERN12><<<grid, 256, 0, s>>>(g->xs, n0, kf, f->L0); break;
+    case GRAPHGP_MATERN32: dense_fill_kernel<GRAPHGP_MATERN32><<<grid, 256, 0, s>>>(g->xs, n0, kf, f->L0); break;
+    case GRAPHGP_MATERN52: dense_fill_kernel<GRAPHGP_MATERN52><<<grid, 256, 0, s>>>(g->xs, n0, kf, f->L0); break;
+    default: dense_fill_kernel<GRAPHGP_SQEXP><<<grid, 256, 0, s>>>(g->xs, n0, kf, f->L0); break;
+  }
+  GGP_CUDA(cudaGetLastError());
+  dense_chol_kernel<<<1, 1024, n0 * sizeof(float), s>>>(f->L0, f->L0inv, n0, f->sigma, f->logdet,
+                                                        f->not_pd);
+  GGP_CUDA(cudaGetLastError());
+  return GRAPHGP_OK;
+}
+
+}  // namespace ggp
+
+using namespace ggp;
+
+extern "C" int graphgp_factor(graphgp_graph_t g, const graphgp_kernel* kern, void* stream,
+                              graphgp_factor_t* out) {
+  if (!out) return GRAPHGP_ERR_INVALID;
+  *out = nullptr;
+  if (!g || !kern || kern->type < 0 || kern->type > 3 || !(kern->sigma2 > 0) ||
+      !(kern->lengthscale > 0) || !(kern->nugget >= 0))
+    return GRAPHGP_ERR_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  graphgp_factor_t f = new (std::nothrow) graphgp_factor_s();
+  if (!f) return GRAPHGP_ERR_OOM;
+  f->g = g;
+  f->kern = *kern;
+  auto fail = [&](int rc) {
+    f->mem.free_all();
+    delete f;
+    return rc;
+  };
+  int rc = [&]() -> int {
+    GGP_TRY(f->mem.alloc(&f->b, (g->N - g->n0) * g->kp));
+    GGP_TRY(f->mem.alloc(&f->sigma, g->N));
+    GGP_TRY(f->mem.alloc(&f->L0, (int64_t)g->n0 * g->n0));
+    GGP_TRY(f->mem.alloc(&f->L0inv, (int64_t)g->n0 * g->n0));
+    GGP_TRY(f->mem.alloc(&f->logdet, 1));
+    GGP_TRY(f->mem.alloc(&f->not_pd, 1));
+    GGP_CUDA(cudaMemsetAsync(f->logdet, 0, 8, s));
+    GGP_CUDA(cudaMemsetAsync(f->not_pd, 0, 8, s));
+    KernF kf = make_kernf(*kern);
+    GGP_TRY(dense_factor(g, f, kf, kern->type, s));
+    GGP_TRY(point_factor(g, f, kf, kern->type, s));
+    return GRAPHGP_OK;
+  }();
+  if (rc < 0) return fail(rc);
+  *out = f;
+  return GRAPHGP_OK;
+}
+
+extern "C" int graphgp_factor_export(graphgp_factor_t f, float* b_d, float* sigma_d, float* L0_d,
+                                     void* stream) {
+  if (!f) return GRAPHGP_ERR_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  graphgp_graph_t g = f->g;
+  if (b_d && g->N > g->n0)
+    GGP_CUDA(cudaMemcpy2DAsync(b_d, g->k * 4, f->b, g->kp * 4, g->k * 4, g->N - g->n0,
+                               cudaMemcpyDeviceToDevice, s));
+  if (sigma_d)
+    GGP_CUDA(cudaMemcpyAsync(sigma_d, f->sigma, g->N * 4, cudaMemcpyDeviceToDevice, s));
+  if (L0_d)
+    GGP_CUDA(cudaMemcpyAsync(L0_d, f->L0, (int64_t)g->n0 * g->n0 * 4, cudaMemcpyDeviceToDevice, s));
+  return GRAPHGP_OK;
+}
+
+extern "C" void graphgp_factor_destroy(graphgp_factor_t f) {
+  if (!f) return;
+  cudaDeviceSynchronize();
+  f->mem.free_all();
+  delete f;
+}

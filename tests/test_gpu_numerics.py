@@ -1,0 +1,138 @@
+"""GPU factor, sweeps, log-determinant and NLL against the FP64 oracle on the
+same seeded inputs (Sec. 2.1 Eq. 2, Alg. 1, Sec. 3).
+
+Tolerances: norm-wise relative 1e-4 for FP32 vectors (b, v, xi), element-wise
+relative 1e-4 for sigma; the log-determinant reduction is checked to 1e-9
+relative against an FP64 sum of the GPU's own sigma, and end to end against
+the oracle within the bound 2 sum |d sigma_i / sigma_i| that the FP32 sigma
+error implies."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads
+from gpu_util import np_, rel_norm, to_gpu
+
+pytestmark = pytest.mark.gpu
+
+KERNELS = {
+    "m32": (1, 1.0, 0.1, 1e-6),
+    "m12": (0, 1.0, 0.1, 1e-6),
+    "m52": (2, 1.3, 0.12, 1e-5),
+    "se": (3, 1.0, 0.08, 1e-4),
+}
+
+
+def _setup(gg, pts, k, kern, n0=None):
+    want = oracle.build_graph(pts, k, n0)
+    g = gg.build_graph(to_gpu(pts), k, n0=want["n0"])
+    order, _, _ = g.export()
+    assert np.array_equal(np_(order), want["order"])  # same graph (bit-exact)
+    K = oracle.Kernel(*kern)
+    fo = oracle.factor(want["pts_pos"], want["nbr_pos"], k, want["n0"], K)
+    f = gg.factor(g, gg.Kernel(*kern))
+    return g, f, want, fo
+
+
+def _check_factor(gg, g, f, want, fo):
+    b, sigma, L0 = (np_(t) for t in f.export())
+    assert rel_norm(b, fo["b"]) < 1e-4
+    assert np.max(np.abs(sigma / fo["sigma"] - 1.0)) < 1e-4
+    assert rel_norm(L0, fo["L0"]) < 1e-4
+    ld = np_(gg.logdet(f))[0]
+    # reduction: FP64 sum over the GPU's own FP32 sigma
+    own = 2.0 * np.sum(np.log(sigma.astype(np.float64)))
+    assert abs(ld - own) <= 1e-9 * abs(own)
+    # end to end: bounded by the sigma error
+    bound = 2.0 * np.sum(np.abs(sigma / fo["sigma"] - 1.0)) * 1.01 + 1e-9 * abs(fo["logdet"])
+    assert abs(ld - fo["logdet"]) <= bound
+    return sigma
+
+
+@pytest.mark.parametrize("name", sorted(KERNELS))
+def test_tiny_factor_sweeps_logdet(gpu_lib, name):
+    w = workloads.WORKLOADS["tiny"]
+    pts = workloads.uniform_cube(w["N"], w["seed"])
+    g, f, want, fo = _setup(gpu_lib, pts, w["k"], KERNELS[name])
+    _check_factor(gpu_lib, g, f, want, fo)
+    N, k, n0 = g.N, g.k, g.n0
+    xi = workloads.white_noise(N, w["xi_seed"])
+    v_or = oracle.generate(fo, want["nbr_pos"], k, n0, xi.astype(np.float64))
+    v = gpu_lib.generate(g, f, to_gpu(xi))
+    assert rel_norm(np_(v), v_or) < 1e-4
+    # whiten on the same FP32 input
+    v_in = v_or.astype(np.float32)
+    xi_or = oracle.whiten(fo, want["nbr_pos"], k, n0, v_in.astype(np.float64))
+    xi_g = gpu_lib.whiten(g, f, to_gpu(v_in))
+    assert rel_norm(np_(xi_g), xi_or) < 1e-4
+    # round trip on the GPU
+    xi_rt = gpu_lib.whiten(g, f, v)
+    assert rel_norm(np_(xi_rt), xi) < 1e-4
+    # NLL
+    nll_or = oracle.nll(fo, want["nbr_pos"], k, n0, v_in.astype(np.float64))
+    nll_g = np_(gpu_lib.nll(g, f, to_gpu(v_in)))[0]
+    assert abs(nll_g - nll_or) <= 1e-4 * abs(nll_or)
+    st, bad = gpu_lib.sync_status(g, f)
+    assert st == 0 and bad == 0
+
+
+@pytest.mark.parametrize("kind,k", [("gaussian", 16), ("ldr", 16), ("uniform", 32), ("blobs", 5),
+                                    ("uniform", 1)])
+def test_factor_and_sweeps_several_tiles(gpu_lib, kind, k):
+    N = 20_011
+    pts = workloads.cloud(kind, N, 40 + k)
+    kern = (1, 1.0, 0.05, 1e-5)
+    g, f, want, fo = _setup(gpu_lib, pts, k, kern, n0=max(k, 128))
+    _check_factor(gpu_lib, g, f, want, fo)
+    xi = workloads.white_noise(N, 41)
+    v_or = oracle.generate(fo, want["nbr_pos"], k, g.n0, xi.astype(np.float64))
+    v = np_(gpu_lib.generate(g, f, to_gpu(xi)))
+    assert rel_norm(v, v_or) < 1e-4
+    xi_or = oracle.whiten(fo, want["nbr_pos"], k, g.n0, v_or.astype(np.float32).astype(np.float64))
+    xi_g = np_(gpu_lib.whiten(g, f, to_gpu(v_or.astype(np.float32))))
+    assert rel_norm(xi_g, xi_or) < 1e-4
+
+
+def test_all_dense(gpu_lib):
+    """N = n0: the whole field is the dense block (Alg. 1 first line)."""
+    pts = workloads.uniform_cube(300, 5)
+    g, f, want, fo = _setup(gpu_lib, pts, 8, KERNELS["m32"], n0=300)
+    _check_factor(gpu_lib, g, f, want, fo)
+    xi = workloads.white_noise(300, 6)
+    v = np_(gpu_lib.generate(g, f, to_gpu(xi)))
+    assert rel_norm(v, oracle.generate(fo, want["nbr_pos"], 8, 300, xi.astype(np.float64))) < 1e-4
+
+
+def test_duplicate_points_without_nugget_flag_not_pd(gpu_lib):
+    base = workloads.uniform_cube(1000, 9)
+    pts = np.concatenate([base, base])
+    g = gpu_lib.build_graph(to_gpu(pts), 8, n0=8)
+    f = gpu_lib.factor(g, gpu_lib.Kernel(1, 1.0, 0.2, 0.0))
+    st, bad = gpu_lib.sync_status(g, f)
+    assert st == gpu_lib.WARN_NOT_PD and bad > 0
+    _, sigma, _ = f.export()
+    assert torch.isfinite(sigma).all()
+
+
+def test_implied_covariance_monte_carlo(gpu_lib):
+    """Samples v = L xi have covariance L L^T (the Vecchia covariance, Eq. 1):
+    empirical covariance of M GPU samples against the oracle's L L^T."""
+    N, k, M = 24, 4, 20000
+    pts = workloads.uniform_cube(N, 11)
+    want = oracle.build_graph(pts, k, n0=4)
+    g = gpu_lib.build_graph(to_gpu(pts), k, n0=4)
+    fo = oracle.factor(want["pts_pos"], want["nbr_pos"], k, 4, oracle.Kernel(1, 1.0, 0.3, 1e-6))
+    f = gpu_lib.factor(g, gpu_lib.Kernel(1, 1.0, 0.3, 1e-6))
+    L = np.stack([oracle.generate(fo, want["nbr_pos"], k, 4, e) for e in np.eye(N)], axis=1)
+    Kt = L @ L.T
+    rng = np.random.default_rng(12)
+    xis = rng.standard_normal((M, N)).astype(np.float32)
+    out = torch.empty((M, N), device="cuda")
+    xg = to_gpu(xis)
+    for m in range(M):
+        gpu_lib.generate(g, f, xg[m], out=out[m])
+    V = np_(out).astype(np.float64)
+    C = V.T @ V / M
+    tol = 5.0 * np.sqrt((np.outer(np.diag(Kt), np.diag(Kt)) + Kt ** 2) / M)
+    assert np.all(np.abs(C - Kt) <= tol)
