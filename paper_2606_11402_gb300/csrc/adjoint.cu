@@ -20,19 +20,10 @@
 #include <algorithm>
 
 #include "pointfactor.cuh"
+#include "sweepsync.cuh"
 
 namespace ggp {
 namespace {
-
-__device__ __forceinline__ uint32_t ld_acq(const uint32_t* p) {
-  uint32_t v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void st_rel(uint32_t* p, uint32_t v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-__device__ __forceinline__ void fence_sc_gpu() { asm volatile("fence.sc.gpu;" ::: "memory"); }
 
 // ---- children CSR -----------------------------------------------------------
 __global__ void edge_keys_kernel(const int32_t* __restrict__ nbr, int64_t rows, int k, int kp,
@@ -54,37 +45,6 @@ __global__ void rowptr_kernel(const uint32_t* __restrict__ keys, int64_t E, int6
     int64_t prev = e == 0 ? -1 : (int64_t)keys[e - 1];
     int64_t cur = e == E ? N : (int64_t)keys[e];
     for (int64_t q = prev + 1; q <= cur; q++) rowptr[q] = e;
-  }
-}
-
-// Reverse sweep: chunk c may run once every chunk from the first chunk that
-// holds a child of its rows to the last one is complete.
-__global__ void chunk_need_rev_kernel(const int64_t* __restrict__ rowptr,
-                                      const int32_t* __restrict__ cedge, int kp, int64_t n0,
-                                      const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
-                                      int64_t n_chunks, int32_t* __restrict__ need) {
-  __shared__ int32_t smin[8];
-  int64_t c = blockIdx.x;
-  if (c >= n_chunks) return;
-  int32_t m = 0x7fffffff;
-  for (int32_t p = lo[c] + threadIdx.x; p < hi[c]; p += blockDim.x)
-    for (int64_t e = rowptr[p]; e < rowptr[p + 1]; e++)
-      m = min(m, (int32_t)(cedge[e] / kp + n0));
-  for (int o = 16; o; o >>= 1) m = min(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0) smin[threadIdx.x >> 5] = m;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int w = 1; w < (int)(blockDim.x >> 5); w++) m = min(m, smin[w]);
-    int32_t r = 0;
-    if (m != 0x7fffffff) {
-      int64_t a = 0, b = n_chunks - 1;
-      while (a < b) {
-        int64_t mid = (a + b + 1) / 2;
-        if (lo[mid] <= m) a = mid; else b = mid - 1;
-      }
-      r = (int32_t)(n_chunks - a);
-    }
-    need[c] = r;
   }
 }
 
@@ -203,69 +163,43 @@ __global__ void whiten_transpose_kernel(const int64_t* __restrict__ rowptr,
   }
 }
 
-// ---- generate VJP: reverse level sweep (same scheme as the forward sweep,
-// chunks taken from the last one backwards) ----------------------------------------
-__global__ void __launch_bounds__(kSweepChunk) generate_adjoint_kernel(
+// ---- generate VJP: reverse level sweep, deepest level first, one cooperative
+// launch with a grid barrier between levels (children of a level-l row are in
+// deeper levels, all complete once level l+1 is) ----------------------------------
+__global__ void __launch_bounds__(256) generate_adjoint_kernel(
     const int64_t* __restrict__ rowptr, const int32_t* __restrict__ cedge, int kp, int64_t n0,
     const float* __restrict__ b, const float* __restrict__ vbar, float* u,
-    const int32_t* __restrict__ chunk_lo, const int32_t* __restrict__ chunk_hi,
-    const int32_t* __restrict__ need_rev, int64_t n_chunks, uint32_t* sync, uint32_t* err,
-    int64_t max_spin) {
-  __shared__ int s_chunk;
-  __shared__ int s_abort;
-  uint32_t* ticket = sync;
-  uint32_t* water = sync + 1;  // trailing complete chunks
-  uint32_t* done = sync + 2;
-  const int tid = threadIdx.x;
-  while (true) {
-    if (tid == 0) s_chunk = (int)atomicAdd(ticket, 1u);
-    __syncthreads();
-    const int64_t t = s_chunk;
-    if (t >= n_chunks) break;
-    const int64_t c = n_chunks - 1 - t;
-    const int32_t lo = chunk_lo[c], hi = chunk_hi[c];
-    const uint32_t need = (uint32_t)need_rev[c];
-    const int64_t p = (int64_t)lo + tid;
-    const bool act = p < hi;
+    const int64_t* __restrict__ level_off, int num_levels, LevelBarrier lb) {
+  __shared__ int s_flag;
+  const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
+  const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint64_t pol_u = l2_evict_last();
+  for (int l = num_levels - 1; l >= 1; l--) {
+    const int64_t hi = level_off[l + 1];
+    int64_t p = level_off[l] + gtid;
     float acc = 0.0f;
     int64_t e0 = 0, e1 = 0;
-    if (act) {
+    if (p < hi) {
       acc = vbar[p];
       e0 = rowptr[p];
       e1 = rowptr[p + 1];
     }
-    if (tid == 0) {
-      int abort = 0;
-      if (ld_acq(water) < need) {
-        int64_t spins = 0;
-        while (ld_acq(water) < need) {
-          if (ld_acq(err) & ERRBIT_TIMEOUT) { abort = 1; break; }
-          if (++spins > max_spin) {
-            atomicOr(err, ERRBIT_TIMEOUT);
-            abort = 1;
-            break;
-          }
-          __nanosleep(64);
-        }
+    if (l < num_levels - 1 && lb.wait(l + 1, gridDim.x, &s_flag)) return;
+    while (p < hi) {
+      for (int64_t e = e0; e < e1; e++) {
+        int32_t ce = cedge[e];
+        acc = fmaf(b[ce], ld_coherent_f(u + (ce / kp + n0), pol_u), acc);
       }
-      s_abort = abort;
+      st_keep_f(u + p, acc, pol_u);
+      p += gsz;
+      if (p < hi) {
+        acc = vbar[p];
+        e0 = rowptr[p];
+        e1 = rowptr[p + 1];
+      }
     }
     __syncthreads();
-    if (s_abort) break;
-    for (int64_t e = e0; e < e1; e++) {
-      int32_t ce = cedge[e];
-      acc = fmaf(b[ce], __ldcg(u + (ce / kp + n0)), acc);
-    }
-    if (act) __stcg(u + p, acc);
-    __syncthreads();
-    if (tid == 0) {
-      fence_sc_gpu();
-      st_rel(done + c, 1u);
-      fence_sc_gpu();
-      uint32_t w = ld_acq(water), w0 = w;
-      while (w < (uint32_t)n_chunks && ld_acq(done + (n_chunks - 1 - w))) w++;
-      if (w > w0) atomicMax(water, w);
-    }
+    lb.arrive(l);
   }
 }
 
@@ -446,7 +380,6 @@ int build_child_csr(graphgp_graph_t g, cudaStream_t s) {
   ChildCSR c;
   GGP_TRY(g->mem.alloc(&c.rowptr, g->N + 1));
   GGP_TRY(g->mem.alloc(&c.child, E));
-  GGP_TRY(g->mem.alloc(&c.need_rev, g->n_chunks));
   c.edges = E;
   Scratch sc(s);
   if (E > 0) {
@@ -463,12 +396,6 @@ int build_child_csr(graphgp_graph_t g, cudaStream_t s) {
     GGP_CUDA(cudaGetLastError());
   } else {
     GGP_CUDA(cudaMemsetAsync(c.rowptr, 0, (g->N + 1) * sizeof(int64_t), s));
-  }
-  if (g->n_chunks) {
-    chunk_need_rev_kernel<<<(unsigned)g->n_chunks, 256, 0, s>>>(c.rowptr, c.child, g->kp, g->n0,
-                                                                g->chunk_lo, g->chunk_hi,
-                                                                g->n_chunks, c.need_rev);
-    GGP_CUDA(cudaGetLastError());
   }
   GGP_CUDA(cudaStreamSynchronize(s));
   g->csr = c;
@@ -497,18 +424,23 @@ int run_generate_backward(graphgp_graph_t g, graphgp_factor_t f, const float* xi
   GGP_TRY(build_child_csr(g, s));
   float* u = g->tmp_vec;
   int n0 = g->n0;
-  if (g->n_chunks) {
-    GGP_CUDA(cudaMemsetAsync(g->sweep_sync, 0, (2 + g->n_chunks) * sizeof(uint32_t), s));
-    static int bps = 0;
-    if (!bps) {
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, generate_adjoint_kernel, kSweepChunk, 0);
-      if (bps < 1) bps = 1;
-    }
-    int64_t grid = std::min<int64_t>((int64_t)num_sms() * bps, g->n_chunks);
-    generate_adjoint_kernel<<<(unsigned)grid, kSweepChunk, 0, s>>>(
-        g->csr.rowptr, g->csr.child, g->kp, n0, f->b, vbar, u, g->chunk_lo, g->chunk_hi,
-        g->csr.need_rev, g->n_chunks, g->sweep_sync, g->err, g->max_spin);
-    GGP_CUDA(cudaGetLastError());
+  if (g->num_levels > 1) {
+    GGP_CUDA(cudaMemsetAsync(g->level_bar, 0, g->num_levels * sizeof(uint32_t), s));
+    static int max_grid = 0;
+    if (!max_grid) max_grid = coop_grid(generate_adjoint_kernel, 256);
+    int grid = (int)std::min<int64_t>(max_grid, std::max<int64_t>((g->max_level_size + 255) / 256, 1));
+    LevelBarrier lb{g->level_bar, g->err, g->max_spin};
+    const int64_t* rp = g->csr.rowptr;
+    const int32_t* ce = g->csr.child;
+    int kp = g->kp;
+    int64_t n0l = n0;
+    const float* bw = f->b;
+    const int64_t* lo = g->level_off_d;
+    int nl = g->num_levels;
+    void* args[] = {(void*)&rp, (void*)&ce, (void*)&kp, (void*)&n0l, (void*)&bw, (void*)&vbar,
+                    (void*)&u,  (void*)&lo, (void*)&nl, (void*)&lb};
+    GGP_CUDA(cudaLaunchCooperativeKernel((const void*)generate_adjoint_kernel, dim3(grid),
+                                         dim3(256), args, 0, s));
   }
   dense_children_kernel<<<(n0 + 255) / 256, 256, 0, s>>>(g->csr.rowptr, g->csr.child, g->kp, n0,
                                                          f->b, vbar, u);

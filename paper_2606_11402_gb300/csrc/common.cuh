@@ -102,15 +102,14 @@ struct Scratch {
 // point at position 0 with weight 0.
 inline int row_stride(int k) { return (k + 3) & ~3; }
 
-// Points per chunk of the level sweeps; chunks never straddle a depth level.
-constexpr int kSweepChunk = 256;
+// Spatial tile of the whiten sweep: this many consecutive k-d in-order ranks.
+constexpr int64_t kTileR = 4096;
 
 // Children (transposed graph) in CSR form, built on first use by the
 // adjoint sweeps.
 struct ChildCSR {
   int64_t* rowptr = nullptr;    // [N+1]
   int32_t* child = nullptr;     // [E] entry (row * kp + slot) of the child's row
-  int32_t* need_rev = nullptr;  // [n_chunks] trailing chunks a chunk waits for
   int64_t edges = 0;
 };
 
@@ -128,13 +127,13 @@ struct graphgp_graph_s {
   int32_t* nbr = nullptr;      // [(N-n0)*kp] positions, nearest first
   std::vector<int64_t> level_off_h;  // [num_levels+1]
   int64_t* level_off_d = nullptr;
-  // sweep chunks (levels >= 1)
-  int64_t n_chunks = 0;
-  int32_t* chunk_lo = nullptr;    // [n_chunks]
-  int32_t* chunk_hi = nullptr;    // [n_chunks]
-  int32_t* chunk_need = nullptr;  // [n_chunks] chunks that must be complete
-  int32_t* chunk_level = nullptr; // [n_chunks]
-  uint32_t* sweep_sync = nullptr; // [2 + n_chunks]: ticket, watermark, done
+  int64_t max_level_size = 0;     // largest depth level >= 1
+  uint32_t* level_bar = nullptr;  // [num_levels] arrivals of the sweep barrier
+  // spatial tiles of the whiten sweep: tile t holds the positions whose
+  // spatial key (k-d in-order rank) lies in [t R, (t+1) R); inside every level
+  // those positions are contiguous, starting at tile_start[t * num_levels + l]
+  int64_t tile_R = 0, n_tiles = 0;
+  int32_t* tile_start = nullptr;  // [(n_tiles + 1) * num_levels]
   uint32_t* err = nullptr;        // device error word
   // tree (graphs built here only)
   bool has_tree = false;
@@ -259,7 +258,8 @@ int knn_query(const float* pts, const int32_t* tree_point,
               int64_t N, int k, int64_t n0, int32_t* nbr_tree, uint32_t* err,
               cudaStream_t s);
 
-int graph_finish_device(graphgp_graph_t g, cudaStream_t s);  // chunks + sync
+// levels, checks and whiten tiles; have_keys: tmp_vec holds in-order keys
+int graph_finish_device(graphgp_graph_t g, cudaStream_t s, bool have_keys);
 
 int dense_factor(graphgp_graph_t g, graphgp_factor_t f, const KernF& kp,
                  int type, cudaStream_t s);

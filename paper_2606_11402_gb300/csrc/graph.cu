@@ -1,7 +1,7 @@
 // Graph construction entry points (Sec. 2.2 "Batch construction", Sec. 2.3
 // last paragraph): canonicalised input, k-d tree, preceding kNN, depth by the
 // parallel fixed point, depth-sorted graph order, relabelled neighbour rows,
-// and the chunk tables of the level sweeps.  Also import / export / save /
+// and the level tables of the sweeps.  Also import / export / save /
 // load / info / destroy of graph handles.
 #include <algorithm>
 #include <cmath>
@@ -87,13 +87,15 @@ __global__ void depth_keys_kernel(const int32_t* __restrict__ node_at_inorder,
 
 __global__ void positions_kernel(const uint32_t* __restrict__ tree_of_pos,
                                  const int32_t* __restrict__ tree_point,
+                                 const int32_t* __restrict__ inorder,
                                  const float* __restrict__ pts, int64_t N,
                                  int32_t* __restrict__ pos_of_tree, int32_t* __restrict__ order,
-                                 float4* __restrict__ xs) {
+                                 float4* __restrict__ xs, int32_t* __restrict__ pos_key) {
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < N;
        p += (int64_t)gridDim.x * blockDim.x) {
     int32_t j = (int32_t)tree_of_pos[p];
     pos_of_tree[j] = (int32_t)p;
+    pos_key[p] = inorder[j];
     int64_t o = tree_point[j];
     order[p] = (int32_t)o;
     xs[p] = make_float4(pts[3 * o], pts[3 * o + 1], pts[3 * o + 2], 0.0f);
@@ -127,39 +129,59 @@ __global__ void order_xs_kernel(const float* __restrict__ pts, const int32_t* __
   }
 }
 
-// Chunk c may run once every chunk before chunk_need[c] is complete: the
-// chunk holding the largest neighbour position of its rows, plus one.  Also
-// checks that no row depends on its own chunk or a later one.
-__global__ void chunk_need_kernel(const int32_t* __restrict__ nbr, int kp, int k, int64_t n0,
-                                  const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
-                                  int64_t n_chunks, int32_t* __restrict__ need,
-                                  uint32_t* __restrict__ err) {
-  __shared__ int32_t smax[8];
-  int64_t c = blockIdx.x;
-  if (c >= n_chunks) return;
-  int32_t l0 = lo[c], h0 = hi[c];
-  int32_t m = -1;
-  for (int32_t p = l0 + threadIdx.x; p < h0; p += blockDim.x) {
-    const int32_t* row = nbr + (p - n0) * kp;
-    for (int a = 0; a < k; a++) m = max(m, row[a]);
-  }
-  for (int o = 16; o; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0) smax[threadIdx.x >> 5] = m;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int w = 1; w < (int)(blockDim.x >> 5); w++) m = max(m, smax[w]);
-    if (m >= l0) atomicOr(err, ERRBIT_INDEX);
-    int32_t r = 0;
-    if (m >= n0) {
-      // last chunk whose start is <= m
-      int64_t a = 0, b = n_chunks - 1;
-      while (a < b) {
-        int64_t mid = (a + b + 1) / 2;
-        if (lo[mid] <= m) a = mid; else b = mid - 1;
-      }
-      r = (int32_t)(a + 1);
+// Every neighbour of a row must lie in an earlier depth level (Sec. 2.2:
+// points of one batch never condition on each other).  Flags ERRBIT_INDEX.
+__global__ void check_levels_kernel(const int32_t* __restrict__ nbr, int kp, int k, int64_t n0,
+                                    const int64_t* __restrict__ level_off, int num_levels,
+                                    int64_t N, uint32_t* __restrict__ err) {
+  for (int64_t p = n0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < N;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    int a0 = 1, b0 = num_levels - 1;  // level of p: last l with level_off[l] <= p
+    while (a0 < b0) {
+      int mid = (a0 + b0 + 1) / 2;
+      if (level_off[mid] <= p) a0 = mid; else b0 = mid - 1;
     }
-    need[c] = r;
+    int64_t start = level_off[a0];
+    const int32_t* row = nbr + (p - n0) * kp;
+    for (int a = 0; a < k; a++)
+      if (row[a] < 0 || row[a] >= start) atomicOr(err, ERRBIT_INDEX);
+  }
+}
+
+// Spatial key of a position when no k-d tree is known (imported graphs):
+// its rank inside its level scaled to [0, N), so every level spans the same
+// key range.
+__global__ void proportional_keys_kernel(const int64_t* __restrict__ level_off, int num_levels,
+                                         int64_t N, int32_t* __restrict__ key) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < N;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    int a0 = 0, b0 = num_levels - 1;
+    while (a0 < b0) {
+      int mid = (a0 + b0 + 1) / 2;
+      if (level_off[mid] <= p) a0 = mid; else b0 = mid - 1;
+    }
+    int64_t lo = level_off[a0], n = level_off[a0 + 1] - lo;
+    key[p] = (int32_t)((p - lo) * N / n);
+  }
+}
+
+// tile_start[t * L + l] = first position of level l whose key is >= t R (keys
+// are ascending inside every level).
+__global__ void tile_table_kernel(const int32_t* __restrict__ key,
+                                  const int64_t* __restrict__ level_off, int num_levels,
+                                  int64_t n_tiles, int64_t R, int32_t* __restrict__ tile_start) {
+  int64_t total = (n_tiles + 1) * num_levels;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t t = e / num_levels;
+    int l = (int)(e - t * num_levels);
+    int64_t a0 = level_off[l], b0 = level_off[l + 1];
+    int64_t target = t * R;
+    while (a0 < b0) {
+      int64_t mid = (a0 + b0) / 2;
+      if ((int64_t)key[mid] < target) a0 = mid + 1; else b0 = mid;
+    }
+    tile_start[e] = (int32_t)a0;
   }
 }
 
@@ -176,35 +198,34 @@ int alloc_common(graphgp_graph_t g) {
 
 }  // namespace
 
-// Chunk tables of the sweeps and their synchronisation words.
-int graph_finish_device(graphgp_graph_t g, cudaStream_t s) {
-  std::vector<int32_t> lo, hi, lv;
-  for (int l = 1; l < g->num_levels; l++) {
-    for (int64_t p = g->level_off_h[l]; p < g->level_off_h[l + 1]; p += kSweepChunk) {
-      lo.push_back((int32_t)p);
-      hi.push_back((int32_t)std::min<int64_t>(p + kSweepChunk, g->level_off_h[l + 1]));
-      lv.push_back(l);
-    }
-  }
-  g->n_chunks = (int64_t)lo.size();
+// Level offsets on the device, the sweep barrier counters, and a check that
+// every neighbour lies in an earlier level.
+int graph_finish_device(graphgp_graph_t g, cudaStream_t s, bool have_keys) {
+  g->max_level_size = 0;
+  for (int l = 1; l < g->num_levels; l++)
+    g->max_level_size = std::max<int64_t>(g->max_level_size, g->level_off_h[l + 1] - g->level_off_h[l]);
   GGP_TRY(g->mem.alloc(&g->level_off_d, g->num_levels + 1));
-  GGP_TRY(g->mem.alloc(&g->chunk_lo, g->n_chunks));
-  GGP_TRY(g->mem.alloc(&g->chunk_hi, g->n_chunks));
-  GGP_TRY(g->mem.alloc(&g->chunk_need, g->n_chunks));
-  GGP_TRY(g->mem.alloc(&g->chunk_level, g->n_chunks));
-  GGP_TRY(g->mem.alloc(&g->sweep_sync, 2 + g->n_chunks));
+  GGP_TRY(g->mem.alloc(&g->level_bar, g->num_levels));
   GGP_CUDA(cudaMemcpyAsync(g->level_off_d, g->level_off_h.data(),
                            (g->num_levels + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
-  if (g->n_chunks) {
-    GGP_CUDA(cudaMemcpyAsync(g->chunk_lo, lo.data(), lo.size() * 4, cudaMemcpyHostToDevice, s));
-    GGP_CUDA(cudaMemcpyAsync(g->chunk_hi, hi.data(), hi.size() * 4, cudaMemcpyHostToDevice, s));
-    GGP_CUDA(cudaMemcpyAsync(g->chunk_level, lv.data(), lv.size() * 4, cudaMemcpyHostToDevice, s));
-    chunk_need_kernel<<<(unsigned)g->n_chunks, 256, 0, s>>>(g->nbr, g->kp, g->k, g->n0, g->chunk_lo,
-                                                            g->chunk_hi, g->n_chunks, g->chunk_need,
-                                                            g->err);
+  if (g->N > g->n0) {
+    check_levels_kernel<<<grid_for(g->N - g->n0, 256), 256, 0, s>>>(
+        g->nbr, g->kp, g->k, g->n0, g->level_off_d, g->num_levels, g->N, g->err);
     GGP_CUDA(cudaGetLastError());
   }
-  // the host vectors must outlive the copies
+  // spatial tiles of the whiten sweep; the keys sit in tmp_vec
+  int32_t* key = (int32_t*)g->tmp_vec;
+  if (!have_keys) {
+    proportional_keys_kernel<<<grid_for(g->N, 256), 256, 0, s>>>(g->level_off_d, g->num_levels,
+                                                                 g->N, key);
+    GGP_CUDA(cudaGetLastError());
+  }
+  g->tile_R = kTileR;
+  g->n_tiles = (g->N + kTileR - 1) / kTileR;
+  GGP_TRY(g->mem.alloc(&g->tile_start, (g->n_tiles + 1) * g->num_levels));
+  tile_table_kernel<<<grid_for((g->n_tiles + 1) * g->num_levels, 256), 256, 0, s>>>(
+      key, g->level_off_d, g->num_levels, g->n_tiles, kTileR, g->tile_start);
+  GGP_CUDA(cudaGetLastError());
   GGP_CUDA(cudaStreamSynchronize(s));
   uint32_t err = 0;
   GGP_CUDA(cudaMemcpy(&err, g->err, 4, cudaMemcpyDeviceToHost));
@@ -319,8 +340,9 @@ extern "C" int graphgp_build_graph(const float* points_d, int64_t N, int d, int 
     GGP_TRY(radix_sort_pairs(keys, vals, keys_s, tree_of_pos, N, bits, s));
     int32_t* pos_of_tree = nullptr;
     GGP_TRY(sc.alloc(&pos_of_tree, N));
-    positions_kernel<<<grid_for(N, 256), 256, 0, s>>>(tree_of_pos, g->tree_point, g->pts_in, N,
-                                                      pos_of_tree, g->order, g->xs);
+    positions_kernel<<<grid_for(N, 256), 256, 0, s>>>(tree_of_pos, g->tree_point, g->inorder,
+                                                      g->pts_in, N, pos_of_tree, g->order, g->xs,
+                                                      (int32_t*)g->tmp_vec);
     GGP_CUDA(cudaGetLastError());
     if (N > n0) {
       relabel_kernel<<<grid_for((N - n0) * g->kp, 256), 256, 0, s>>>(
@@ -336,7 +358,7 @@ extern "C" int graphgp_build_graph(const float* points_d, int64_t N, int d, int 
     return GRAPHGP_OK;
   }();
   if (rc < 0) return fail(rc);
-  rc = graph_finish_device(g, s);
+  rc = graph_finish_device(g, s, true);
   if (rc < 0) return fail(rc);
   *out = g;
   return GRAPHGP_OK;
@@ -411,7 +433,7 @@ extern "C" int graphgp_graph_import(const float* points_h, int64_t N, int k, int
     return GRAPHGP_OK;
   }();
   if (rc < 0) return fail(rc);
-  rc = graph_finish_device(g, s);
+  rc = graph_finish_device(g, s, false);
   if (rc < 0) return fail(rc);
   *out = g;
   return GRAPHGP_OK;

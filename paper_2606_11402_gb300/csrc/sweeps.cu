@@ -1,36 +1,25 @@
 // Level sweeps of Alg. 1 (generate, v = L xi) and the inverse application
 // and log-determinant of Sec. 3 (whiten, xi = L^-1 v; logdet; NLL).
 //
-// generate: v_0 = L0 xi_0 for the dense block, then for every position i of
-// depth >= 1: v_i = b_i . v_c(i) + sigma_i xi_i, where every neighbour lies in
-// an earlier depth level.  One persistent launch walks all levels without a
-// grid barrier: blocks take chunks of 256 consecutive positions in order from
-// a ticket counter, issue the loads of their rows (neighbour indices,
-// weights, sigma, xi) at once, then wait until every chunk their rows depend
-// on is complete -- a watermark W counts the leading complete chunks -- and
-// then gather.  Chunks are claimed in increasing order and each depends only
-// on earlier chunks, so the lowest unfinished chunk can always run.  Every
-// wait is bounded; on expiry the kernel records ERR_TIMEOUT and all blocks
-// leave.
+// generate: v_0 = L0 xi_0 for the dense block, then batch by batch
+// (Sec. 2.2: points of one depth level are conditionally independent)
+// v_i = b_i . v_c(i) + sigma_i xi_i; every neighbour lies in an earlier level.
+// One cooperative launch walks all levels with a grid-wide barrier between
+// consecutive levels (sweepsync.cuh); each thread loads the neighbour row,
+// weights, sigma and xi of its next point before waiting, so the row stream
+// overlaps the barrier and only the gathers of v wait for it.
 //
 // whiten: xi_i = (v_i - b_i . v_c(i)) / sigma_i has no dependencies; one
-// streaming launch (plus xi_0 = L0^-1 v_0 for the dense block).
-#include "common.cuh"
+// streaming launch in position order (plus xi_0 = L0^-1 v_0 for the dense
+// block).  Positions are level-major and spatially sorted inside a level, and
+// neighbours sit a few levels back, so the gathered v lines stay in L2 when
+// the row stream is marked evict-first and v evict-last.
+#include <algorithm>
+
+#include "sweepsync.cuh"
 
 namespace ggp {
 namespace {
-
-__device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
-  uint32_t v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-__device__ __forceinline__ void st_release(uint32_t* p, uint32_t v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-__device__ __forceinline__ void fence_sc() { asm volatile("fence.sc.gpu;" ::: "memory"); }
 
 // y[i] = sum_{m <= i} M[i][m] x[m] for the n0 x n0 lower-triangular M; one
 // warp per row.  Optionally accumulates sum y_i^2 in FP64.
@@ -59,30 +48,31 @@ struct Row {
 
 template <int KP>
 __device__ __forceinline__ void load_row(Row<KP>& r, const int32_t* __restrict__ nbr,
-                                         const float* __restrict__ b, int64_t row) {
+                                         const float* __restrict__ b, int64_t row, uint64_t pol) {
   const int4* np = reinterpret_cast<const int4*>(nbr + row * KP);
   const float4* bp = reinterpret_cast<const float4*>(b + row * KP);
 #pragma unroll
   for (int q = 0; q < KP / 4; q++) {
-    r.n[q] = __ldcs(np + q);
-    r.w[q] = __ldcs(bp + q);
+    r.n[q] = ld_stream_i4(np + q, pol);
+    r.w[q] = ld_stream_f4(bp + q, pol);
   }
 }
 
-// sum_a b_a v[c_a]; gathered through L2 (.cg) because v is written by other
-// blocks during the sweep.
-template <int KP, bool COHERENT>
-__device__ __forceinline__ float gather_dot(const Row<KP>& r, const float* __restrict__ v) {
+// sum_a b_a v[c_a].  LEVEL: v is written level by level in the same launch;
+// the gathered entries belong to earlier levels, published by the barrier.
+template <int KP, bool LEVEL>
+__device__ __forceinline__ float gather_dot(const Row<KP>& r, const float* __restrict__ v,
+                                            uint64_t pol) {
   float acc0 = 0.0f, acc1 = 0.0f;
 #pragma unroll
   for (int q = 0; q < KP / 4; q++) {
     float v0, v1, v2, v3;
-    if (COHERENT) {
-      v0 = __ldcg(v + r.n[q].x); v1 = __ldcg(v + r.n[q].y);
-      v2 = __ldcg(v + r.n[q].z); v3 = __ldcg(v + r.n[q].w);
+    if (LEVEL) {
+      v0 = ld_level_f(v + r.n[q].x, pol); v1 = ld_level_f(v + r.n[q].y, pol);
+      v2 = ld_level_f(v + r.n[q].z, pol); v3 = ld_level_f(v + r.n[q].w, pol);
     } else {
-      v0 = __ldg(v + r.n[q].x); v1 = __ldg(v + r.n[q].y);
-      v2 = __ldg(v + r.n[q].z); v3 = __ldg(v + r.n[q].w);
+      v0 = ld_keep_f(v + r.n[q].x, pol); v1 = ld_keep_f(v + r.n[q].y, pol);
+      v2 = ld_keep_f(v + r.n[q].z, pol); v3 = ld_keep_f(v + r.n[q].w, pol);
     }
     acc0 = fmaf(r.w[q].x, v0, acc0);
     acc1 = fmaf(r.w[q].y, v1, acc1);
@@ -92,72 +82,43 @@ __device__ __forceinline__ float gather_dot(const Row<KP>& r, const float* __res
   return acc0 + acc1;
 }
 
-constexpr int kSweepThreads = kSweepChunk;  // one position per thread
+constexpr int kSweepThreads = 256;
 
 template <int KP>
 __global__ void __launch_bounds__(kSweepThreads) generate_kernel(
     const int32_t* __restrict__ nbr, const float* __restrict__ b, const float* __restrict__ sigma,
-    const float* __restrict__ xi, float* v, const int32_t* __restrict__ chunk_lo,
-    const int32_t* __restrict__ chunk_hi, const int32_t* __restrict__ chunk_need,
-    int64_t n_chunks, int64_t n0, uint32_t* sync, uint32_t* err, int64_t max_spin) {
-  __shared__ int s_chunk;
-  __shared__ int s_abort;
-  uint32_t* ticket = sync;
-  uint32_t* water = sync + 1;
-  uint32_t* done = sync + 2;
-  const int tid = threadIdx.x;
-  while (true) {
-    if (tid == 0) s_chunk = (int)atomicAdd(ticket, 1u);
-    __syncthreads();
-    const int64_t c = s_chunk;
-    if (c >= n_chunks) break;
-    const int32_t lo = chunk_lo[c], hi = chunk_hi[c];
-    const uint32_t need = (uint32_t)chunk_need[c];
-    const int64_t pos = (int64_t)lo + tid;
-    const bool act = pos < hi;
+    const float* __restrict__ xi, float* v, const int64_t* __restrict__ level_off,
+    int num_levels, int64_t n0, LevelBarrier lb) {
+  __shared__ int s_flag;
+  const uint64_t pol_rows = l2_evict_first();
+  const uint64_t pol_v = l2_evict_last();
+  for (int l = 1; l < num_levels; l++) {
+    // each block takes one contiguous, spatially compact slice of the level
+    const int64_t lo = level_off[l], n = level_off[l + 1] - lo;
+    const int64_t per = (n + gridDim.x - 1) / gridDim.x;
+    const int64_t b0 = lo + min((int64_t)blockIdx.x * per, n);
+    const int64_t hi = lo + min((int64_t)(blockIdx.x + 1) * per, n);
+    int64_t p = b0 + threadIdx.x;
     Row<KP> r;
     float sg = 0.0f, x = 0.0f;
-    if (act) {
-      load_row<KP>(r, nbr, b, pos - n0);
-      sg = __ldcs(sigma + pos);
-      x = __ldcs(xi + pos);
+    if (p < hi) {
+      load_row<KP>(r, nbr, b, p - n0, pol_rows);
+      sg = ld_stream_f(sigma + p, pol_rows);
+      x = ld_stream_f(xi + p, pol_rows);
     }
-    if (tid == 0) {
-      int abort = 0;
-      if (ld_acquire(water) < need) {
-        int64_t spins = 0;
-        while (ld_acquire(water) < need) {
-          if (ld_acquire(err) & ERRBIT_TIMEOUT) {
-            abort = 1;
-            break;
-          }
-          if (++spins > max_spin) {
-            atomicOr(err, ERRBIT_TIMEOUT);
-            abort = 1;
-            break;
-          }
-          __nanosleep(64);
-        }
+    if (l > 1 && lb.wait(l - 1, gridDim.x, &s_flag)) return;
+    while (p < hi) {
+      float acc = gather_dot<KP, true>(r, v, pol_v);
+      st_keep_f(v + p, fmaf(sg, x, acc), pol_v);
+      p += blockDim.x;
+      if (p < hi) {
+        load_row<KP>(r, nbr, b, p - n0, pol_rows);
+        sg = ld_stream_f(sigma + p, pol_rows);
+        x = ld_stream_f(xi + p, pol_rows);
       }
-      s_abort = abort;
     }
     __syncthreads();
-    if (s_abort) break;
-    if (act) {
-      float acc = gather_dot<KP, true>(r, v);
-      __stcg(v + pos, fmaf(sg, x, acc));
-    }
-    __syncthreads();
-    if (tid == 0) {
-      fence_sc();
-      st_release(done + c, 1u);
-      fence_sc();
-      // advance the watermark over the leading complete chunks
-      uint32_t w = ld_acquire(water);
-      uint32_t w0 = w;
-      while (w < (uint32_t)n_chunks && ld_acquire(done + w)) w++;
-      if (w > w0) atomicMax(water, w);
-    }
+    lb.arrive(l);
   }
 }
 
@@ -166,17 +127,98 @@ __global__ void __launch_bounds__(256) whiten_kernel(
     const int32_t* __restrict__ nbr, const float* __restrict__ b, const float* __restrict__ sigma,
     const float* __restrict__ v, float* __restrict__ xi, int64_t N, int64_t n0,
     double* __restrict__ sq) {
+  const uint64_t pol_rows = l2_evict_first();
+  const uint64_t pol_v = l2_evict_last();
   double local = 0.0;
   for (int64_t pos = n0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; pos < N;
        pos += (int64_t)gridDim.x * blockDim.x) {
     Row<KP> r;
-    load_row<KP>(r, nbr, b, pos - n0);
-    float sg = __ldcs(sigma + pos);
-    float vi = __ldcs(v + pos);
-    float acc = gather_dot<KP, false>(r, v);
+    load_row<KP>(r, nbr, b, pos - n0, pol_rows);
+    float sg = ld_stream_f(sigma + pos, pol_rows);
+    float vi = ld_keep_f(v + pos, pol_v);
+    float acc = gather_dot<KP, false>(r, v, pol_v);
     float out = (vi - acc) / sg;
-    __stcs(xi + pos, out);
+    st_stream_f(xi + pos, out, pol_rows);
     if (sq) local += (double)out * (double)out;
+  }
+  if (sq) {
+    __shared__ double red[8];
+    for (int o = 16; o; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = local;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double s = 0.0;
+      for (int i = 0; i < (int)(blockDim.x >> 5); i++) s += red[i];
+      atomicAdd(sq, s);
+    }
+  }
+}
+
+// whiten over spatial tiles: a block takes one tile (a k-d in-order rank range
+// of kTileR points) and walks its positions in every level >= 1.  The gathers
+// of a tile land mostly on the same tile's v values, which stay in L1.
+template <int KP>
+__global__ void __launch_bounds__(256) whiten_tiles_kernel(
+    const int32_t* __restrict__ nbr, const float* __restrict__ b, const float* __restrict__ sigma,
+    const float* __restrict__ v, float* __restrict__ xi, int64_t n0,
+    const int32_t* __restrict__ tile_start, int64_t n_tiles, int num_levels,
+    double* __restrict__ sq) {
+  extern __shared__ int32_t sm[];
+  int32_t* s_start = sm;               // [num_levels]
+  int32_t* s_pref = sm + num_levels;   // [num_levels + 1]
+  __shared__ int32_t s_carry;
+  const uint64_t pol_rows = l2_evict_first();
+  const uint64_t pol_v = l2_evict_last();
+  double local = 0.0;
+  for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+    const int32_t* ts = tile_start + t * num_levels;
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    // exclusive prefix of the tile's counts over levels 1..L-1 (level 0 is dense)
+    for (int base = 1; base < num_levels; base += blockDim.x) {
+      int l = base + threadIdx.x;
+      int32_t c = 0;
+      if (l < num_levels) {
+        int32_t a0 = ts[l];
+        c = ts[num_levels + l] - a0;
+        s_start[l] = a0;
+      }
+      // block-wide inclusive scan of c
+      int32_t x = c;
+      for (int o = 1; o < 32; o <<= 1) {
+        int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if ((threadIdx.x & 31) >= o) x += y;
+      }
+      __shared__ int32_t wsum[8];
+      if ((threadIdx.x & 31) == 31) wsum[threadIdx.x >> 5] = x;
+      __syncthreads();
+      int32_t wpre = 0;
+      for (int w = 0; w < (int)(threadIdx.x >> 5); w++) wpre += wsum[w];
+      int32_t carry = s_carry;
+      if (l < num_levels) s_pref[l] = carry + wpre + x - c;
+      __syncthreads();
+      if (threadIdx.x == blockDim.x - 1) s_carry = carry + wpre + x;
+      __syncthreads();
+    }
+    const int32_t total = s_carry;
+    for (int32_t vi = threadIdx.x; vi < total; vi += blockDim.x) {
+      // level of vi: last l >= 1 with s_pref[l] <= vi
+      int lo = 1, hi = num_levels - 1;
+      while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (s_pref[mid] <= vi) lo = mid; else hi = mid - 1;
+      }
+      const int64_t pos = (int64_t)s_start[lo] + (vi - s_pref[lo]);
+      Row<KP> r;
+      load_row<KP>(r, nbr, b, pos - n0, pol_rows);
+      float sg = ld_stream_f(sigma + pos, pol_rows);
+      float vv = ld_keep_f(v + pos, pol_v);
+      float acc = gather_dot<KP, false>(r, v, pol_v);
+      float out = (vv - acc) / sg;
+      st_stream_f(xi + pos, out, pol_rows);
+      if (sq) local += (double)out * (double)out;
+    }
+    __syncthreads();
   }
   if (sq) {
     __shared__ double red[8];
@@ -199,20 +241,23 @@ __global__ void nll_finish_kernel(const double* __restrict__ sq, const double* _
 template <int KP>
 int launch_generate(graphgp_graph_t g, graphgp_factor_t f, const float* xi, float* v,
                     cudaStream_t s) {
-  if (g->n_chunks == 0) return GRAPHGP_OK;
-  GGP_CUDA(cudaMemsetAsync(g->sweep_sync, 0, (2 + g->n_chunks) * sizeof(uint32_t), s));
-  static int blocks_per_sm = 0;
-  if (!blocks_per_sm) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, generate_kernel<KP>,
-                                                  kSweepThreads, 0);
-    if (blocks_per_sm < 1) blocks_per_sm = 1;
-  }
-  int64_t grid = (int64_t)num_sms() * blocks_per_sm;
-  if (grid > g->n_chunks) grid = g->n_chunks;
-  generate_kernel<KP><<<(unsigned)grid, kSweepThreads, 0, s>>>(
-      g->nbr, f->b, f->sigma, xi, v, g->chunk_lo, g->chunk_hi, g->chunk_need, g->n_chunks, g->n0,
-      g->sweep_sync, g->err, g->max_spin);
-  GGP_CUDA(cudaGetLastError());
+  if (g->num_levels <= 1) return GRAPHGP_OK;
+  GGP_CUDA(cudaMemsetAsync(g->level_bar, 0, g->num_levels * sizeof(uint32_t), s));
+  static int max_grid = 0;
+  if (!max_grid) max_grid = coop_grid(generate_kernel<KP>, kSweepThreads);
+  int64_t want = (g->max_level_size + kSweepThreads - 1) / kSweepThreads;
+  int grid = (int)std::min<int64_t>(max_grid, std::max<int64_t>(want, 1));
+  LevelBarrier lb{g->level_bar, g->err, g->max_spin};
+  const int32_t* nbr = g->nbr;
+  const float* bw = f->b;
+  const float* sg = f->sigma;
+  const int64_t* lo = g->level_off_d;
+  int nl = g->num_levels;
+  int64_t n0 = g->n0;
+  void* args[] = {(void*)&nbr, (void*)&bw, (void*)&sg, (void*)&xi, (void*)&v,
+                  (void*)&lo,  (void*)&nl, (void*)&n0, (void*)&lb};
+  GGP_CUDA(cudaLaunchCooperativeKernel((const void*)generate_kernel<KP>, dim3(grid),
+                                       dim3(kSweepThreads), args, 0, s));
   return GRAPHGP_OK;
 }
 
@@ -221,8 +266,17 @@ int launch_whiten(graphgp_graph_t g, graphgp_factor_t f, const float* v, float* 
                   cudaStream_t s) {
   int64_t n = g->N - g->n0;
   if (n <= 0) return GRAPHGP_OK;
-  whiten_kernel<KP><<<grid_for(n, 256, 8), 256, 0, s>>>(g->nbr, f->b, f->sigma, v, xi, g->N,
-                                                        g->n0, sq);
+  if (g->tile_start && g->num_levels <= 8192) {
+    size_t smem = (2 * (size_t)g->num_levels + 1) * sizeof(int32_t);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, whiten_tiles_kernel<KP>, 256, smem);
+    int64_t grid = std::min<int64_t>(g->n_tiles, (int64_t)std::max(per_sm, 1) * num_sms());
+    whiten_tiles_kernel<KP><<<(unsigned)grid, 256, smem, s>>>(
+        g->nbr, f->b, f->sigma, v, xi, g->n0, g->tile_start, g->n_tiles, g->num_levels, sq);
+  } else {
+    whiten_kernel<KP><<<grid_for(n, 256, 8), 256, 0, s>>>(g->nbr, f->b, f->sigma, v, xi, g->N,
+                                                          g->n0, sq);
+  }
   GGP_CUDA(cudaGetLastError());
   return GRAPHGP_OK;
 }

@@ -1,0 +1,156 @@
+// Level barrier and L2 cache-policy helpers of the level sweeps.
+//
+// The sweeps of Alg. 1 run as one cooperative launch (all blocks resident)
+// that walks the depth levels in order.  After writing its share of level l a
+// block adds one to count[l] with release semantics; before gathering level
+// l+1 it waits until count[l] equals the number of blocks.  Rows of the next
+// level do not depend on the field, so blocks load them before the wait.
+// Every wait is bounded: after max_spin polls the block sets ERRBIT_TIMEOUT
+// and leaves; a block that sees the bit leaves as well, so the launch ends
+// and the host reads GRAPHGP_ERR_TIMEOUT from graphgp_sync_status.
+#pragma once
+
+#include "common.cuh"
+
+namespace ggp {
+
+__device__ __forceinline__ uint32_t sync_ld_acquire(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+struct LevelBarrier {
+  uint32_t* count;  // [num_levels] arrivals per level
+  uint32_t* err;
+  int64_t max_spin;
+
+  // Call after __syncthreads(): the block's stores of level l are complete.
+  __device__ __forceinline__ void arrive(int l) const {
+    if (threadIdx.x == 0)
+      asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(count + l) : "memory");
+  }
+
+  // Whole block: wait until every block arrived at level l.  Returns nonzero
+  // (uniformly) when the block must leave.
+  __device__ __forceinline__ int wait(int l, uint32_t nblocks, int* s_flag) const {
+    if (threadIdx.x == 0) {
+      int abort = 0;
+      int64_t spins = 0;
+      while (sync_ld_acquire(count + l) < nblocks) {
+        if ((++spins & 63) == 0 && (sync_ld_acquire(err) & ERRBIT_TIMEOUT)) {
+          abort = 1;
+          break;
+        }
+        if (spins > max_spin) {
+          atomicOr(err, ERRBIT_TIMEOUT);
+          abort = 1;
+          break;
+        }
+        __nanosleep(32);
+      }
+      *s_flag = abort;
+    }
+    __syncthreads();
+    return *s_flag;
+  }
+};
+
+// L2 eviction policies.  Streamed rows are read once; the field vector is
+// gathered again by later levels.  GGP_ROW_POLICY / GGP_V_POLICY select the
+// priority: 0 evict_normal, 1 evict_first, 2 evict_last.
+#ifndef GGP_ROW_POLICY
+#define GGP_ROW_POLICY 1
+#endif
+#ifndef GGP_V_POLICY
+#define GGP_V_POLICY 0
+#endif
+
+template <int P>
+__device__ __forceinline__ uint64_t l2_policy() {
+  uint64_t p;
+  if (P == 1)
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  else if (P == 2)
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  else
+    asm("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
+__device__ __forceinline__ uint64_t l2_evict_first() { return l2_policy<GGP_ROW_POLICY>(); }
+__device__ __forceinline__ uint64_t l2_evict_last() { return l2_policy<GGP_V_POLICY>(); }
+
+__device__ __forceinline__ int4 ld_stream_i4(const int4* p, uint64_t pol) {
+  int4 v;
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.s32 {%0,%1,%2,%3}, [%4], %5;"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(p), "l"(pol));
+  return v;
+}
+
+__device__ __forceinline__ float4 ld_stream_f4(const float4* p, uint64_t pol) {
+  float4 v;
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.f32 {%0,%1,%2,%3}, [%4], %5;"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "l"(p), "l"(pol));
+  return v;
+}
+
+__device__ __forceinline__ float ld_stream_f(const float* p, uint64_t pol) {
+  float v;
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.f32 %0, [%1], %2;"
+               : "=f"(v)
+               : "l"(p), "l"(pol));
+  return v;
+}
+
+// read-only input vector, kept in L2
+__device__ __forceinline__ float ld_keep_f(const float* p, uint64_t pol) {
+  float v;
+  asm volatile("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+  return v;
+}
+
+// field values of earlier levels inside a level sweep: cached in L1.  They
+// were written before the level barrier, whose gpu-scope acquire makes them
+// visible, and nothing read during a level is written during that level.
+__device__ __forceinline__ float ld_level_f(const float* p, uint64_t pol) {
+  float v;
+  asm volatile("ld.global.L2::cache_hint.f32 %0, [%1], %2;"
+               : "=f"(v)
+               : "l"(p), "l"(pol)
+               : "memory");
+  return v;
+}
+
+// vector written by other blocks during the launch: read at L2 (coherent)
+__device__ __forceinline__ float ld_coherent_f(const float* p, uint64_t pol) {
+  float v;
+  asm volatile("ld.global.cg.L2::cache_hint.f32 %0, [%1], %2;"
+               : "=f"(v)
+               : "l"(p), "l"(pol)
+               : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_keep_f(float* p, float v, uint64_t pol) {
+  asm volatile("st.global.cg.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(v), "l"(pol)
+               : "memory");
+}
+
+__device__ __forceinline__ void st_stream_f(float* p, float v, uint64_t pol) {
+  asm volatile("st.global.cs.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(v), "l"(pol)
+               : "memory");
+}
+
+// Largest grid of kernel `fn` (block threads, dyn smem) that is co-resident.
+template <class F>
+inline int coop_grid(F fn, int threads, size_t smem = 0) {
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem);
+  if (per_sm < 1) per_sm = 1;
+  return per_sm * num_sms();
+}
+
+}  // namespace ggp

@@ -8,14 +8,15 @@ import torch
 
 import oracle
 import workloads
-from gpu_util import np_, rel_norm, to_gpu
+from gpu_util import fp32_tolerance, np_, rel_norm, to_gpu
 
 pytestmark = pytest.mark.gpu
 
 CASES = [
     ("uniform", 3000, 8, (1, 1.0, 0.1, 1e-4)),
-    ("gaussian", 3000, 16, (3, 1.0, 0.3, 1e-4)),
-    ("uniform", 2500, 32, (3, 1.0, 0.08, 1e-4)),
+    # the differentiation workload's kernel at N = 2^12: SE, l = 0.03, nugget 1e-4, k = 32
+    ("uniform", 4096, 32, (3, 1.0, 0.03, 1e-4)),
+    ("gaussian", 3000, 16, (1, 1.0, 0.1, 1e-6)),
     ("ldr", 3000, 5, (2, 1.2, 0.1, 1e-3)),
 ]
 
@@ -30,9 +31,15 @@ def _setup(gg, kind, N, k, kern):
     return g, f, want, fo, K
 
 
-def _theta_close(got, want):
+def _theta_close(got, want, tol=1e-4):
     scale = np.max(np.abs(want))
-    assert np.all(np.abs(got - want) <= 2e-3 * scale), (got, want)
+    assert np.all(np.abs(got - want) <= max(2e-3, 20 * tol) * scale), (got, want)
+
+
+def _tol(want, kern, k):
+    """1e-4, or the FP32 conditioning bound when the kernel is too smooth for
+    it (the large-dynamic-range cloud's dense core)."""
+    return fp32_tolerance(want, kern)[1]
 
 
 @pytest.mark.parametrize("case", CASES)
@@ -43,8 +50,9 @@ def test_nll_gradient(gpu_lib, case):
                         workloads.white_noise(N, 61).astype(np.float64)).astype(np.float32)
     vbar_or, tb_or = oracle.nll_grad(want, K, v.astype(np.float64))
     vbar, tb = gpu_lib.nll_backward(g, f, to_gpu(v))
-    assert rel_norm(np_(vbar), vbar_or) < 1e-4
-    _theta_close(np_(tb), tb_or)
+    tol = _tol(want, kern, k)
+    assert rel_norm(np_(vbar), vbar_or) < tol
+    _theta_close(np_(tb), tb_or, tol)
 
 
 @pytest.mark.parametrize("case", CASES)
@@ -61,8 +69,9 @@ def test_whiten_vjp(gpu_lib, case):
                                    a["sigbar"])
     xi = gpu_lib.whiten(g, f, to_gpu(v))
     vbar, tb = gpu_lib.whiten_backward(g, f, to_gpu(v), xi, to_gpu(xibar), 0.7)
-    assert rel_norm(np_(vbar), a["vbar"]) < 1e-4
-    _theta_close(np_(tb), tb_or)
+    tol = _tol(want, kern, k)
+    assert rel_norm(np_(vbar), a["vbar"]) < tol
+    _theta_close(np_(tb), tb_or, tol)
 
 
 @pytest.mark.parametrize("case", CASES)
@@ -79,8 +88,9 @@ def test_generate_vjp(gpu_lib, case):
                                    a["sigbar"])
     v = gpu_lib.generate(g, f, to_gpu(xi))
     xibar, tb = gpu_lib.generate_backward(g, f, to_gpu(xi), v, to_gpu(vbar))
-    assert rel_norm(np_(xibar), a["xibar"]) < 1e-4
-    _theta_close(np_(tb), tb_or)
+    tol = _tol(want, kern, k)
+    assert rel_norm(np_(xibar), a["xibar"]) < tol
+    _theta_close(np_(tb), tb_or, tol)
 
 
 def test_thetabar_accumulates(gpu_lib):
@@ -90,3 +100,31 @@ def test_thetabar_accumulates(gpu_lib):
     t2 = t1.clone()
     gpu_lib.nll_backward(g, f, v, thetabar=t2)
     assert torch.allclose(t2, 2 * t1, rtol=1e-6)
+
+
+def _max_cond(want, K, k, rows=200):
+    """Largest condition number of K_cc over sampled rows (numpy, FP64)."""
+    x = want["pts_pos"].astype(np.float64)
+    n0 = want["n0"]
+    out = 0.0
+    for i in np.linspace(n0, want["N"] - 1, rows).astype(int):
+        c = want["nbr_pos"][i - n0]
+        r = np.sqrt(((x[c][:, None] - x[c][None]) ** 2).sum(-1))
+        Kc = np.vectorize(lambda rr: oracle.kappa(K, rr))(r) + K.nugget * np.eye(k)
+        out = max(out, np.linalg.cond(Kc))
+    return out
+
+
+def test_ill_conditioned_kernel_error_scales_with_condition(gpu_lib):
+    """A very smooth kernel (SE, l = 0.3 on a unit-Gaussian cloud) makes K_cc
+    ill conditioned; FP32 kernel evaluation perturbs K by ~2^-24 relative, so
+    the gradient error is bounded by ~cond(K_cc) 2^-24 rather than 1e-4."""
+    g, f, want, fo, K = _setup(gpu_lib, "gaussian", 3000, 16, (3, 1.0, 0.3, 1e-4))
+    cond = _max_cond(want, K, 16)
+    tol = max(1e-4, 4.0 * cond * 2.0 ** -24)
+    v = oracle.generate(fo, want["nbr_pos"], 16, 64,
+                        workloads.white_noise(3000, 61).astype(np.float64)).astype(np.float32)
+    vbar_or, tb_or = oracle.nll_grad(want, K, v.astype(np.float64))
+    vbar, tb = gpu_lib.nll_backward(g, f, to_gpu(v))
+    assert rel_norm(np_(vbar), vbar_or) < tol, (cond, tol)
+    assert np.all(np.abs(np_(tb) - tb_or) <= max(2e-3, tol * 10) * np.abs(tb_or).max())
