@@ -63,7 +63,7 @@ struct LevelBarrier {
 #define GGP_ROW_POLICY 1
 #endif
 #ifndef GGP_V_POLICY
-#define GGP_V_POLICY 0
+#define GGP_V_POLICY 2
 #endif
 
 template <int P>
@@ -83,7 +83,7 @@ __device__ __forceinline__ uint64_t l2_evict_last() { return l2_policy<GGP_V_POL
 
 __device__ __forceinline__ int4 ld_stream_i4(const int4* p, uint64_t pol) {
   int4 v;
-  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.s32 {%0,%1,%2,%3}, [%4], %5;"
+  asm volatile("ld.global.nc.L1::evict_first.L2::cache_hint.v4.s32 {%0,%1,%2,%3}, [%4], %5;"
                : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
                : "l"(p), "l"(pol));
   return v;
@@ -91,7 +91,7 @@ __device__ __forceinline__ int4 ld_stream_i4(const int4* p, uint64_t pol) {
 
 __device__ __forceinline__ float4 ld_stream_f4(const float4* p, uint64_t pol) {
   float4 v;
-  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.f32 {%0,%1,%2,%3}, [%4], %5;"
+  asm volatile("ld.global.nc.L1::evict_first.L2::cache_hint.v4.f32 {%0,%1,%2,%3}, [%4], %5;"
                : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
                : "l"(p), "l"(pol));
   return v;
@@ -99,7 +99,7 @@ __device__ __forceinline__ float4 ld_stream_f4(const float4* p, uint64_t pol) {
 
 __device__ __forceinline__ float ld_stream_f(const float* p, uint64_t pol) {
   float v;
-  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.f32 %0, [%1], %2;"
+  asm volatile("ld.global.nc.L1::evict_first.L2::cache_hint.f32 %0, [%1], %2;"
                : "=f"(v)
                : "l"(p), "l"(pol));
   return v;
