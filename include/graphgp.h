@@ -173,6 +173,22 @@ int graphgp_logdet(graphgp_factor_t f, double* out_d, void* stream);
 int graphgp_nll(graphgp_graph_t g, graphgp_factor_t f, const float* v_d,
                 double* out_d, void* stream);
 
+/* The same value as graphgp_nll, computed without allocating device memory
+ * during the call (the paper has no counterpart; this serves callers that
+ * cannot allocate while they run, e.g. a serving loop that reserved all
+ * device memory for resident graphs up front, or a latency-critical path that
+ * must not pay cudaMalloc's device-wide synchronisation).  The reduction
+ * scratch is a 512 KiB array inside the library, one FP64 slot per whiten
+ * tile (4096 points) plus one: graphs with N > 2^28 points or more than 8192
+ * depth levels are rejected with GRAPHGP_ERR_INVALID.  The array's device
+ * address is looked up on the first call made on each device (make that call
+ * before any stream capture); the array stays allocated on every device that
+ * loaded the library until the process exits.  All calls share it: calls that
+ * overlap on the GPU race, so never run two concurrently on one device.
+ * The final sum runs in a fixed order. */
+int graphgp_nll_noalloc(graphgp_graph_t g, graphgp_factor_t f, const float* v_d,
+                        double* out_d, void* stream);
+
 /* ---- adjoints (Sec. 2.3 "forward and backward derivatives") -------------
  * Vector-Jacobian products.  thetabar_d is double[3] =
  * [d/d lengthscale, d/d sigma2, d/d nugget] and is ACCUMULATED (+=).  The

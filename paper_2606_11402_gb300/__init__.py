@@ -88,6 +88,7 @@ def load() -> ctypes.CDLL:
             "graphgp_whiten": [_P, _P, _P, _P, _P],
             "graphgp_logdet": [_P, _P, _P],
             "graphgp_nll": [_P, _P, _P, _P, _P],
+            "graphgp_nll_noalloc": [_P, _P, _P, _P, _P],
             "graphgp_generate_backward": [_P, _P, _P, _P, _P, _P, _P, _P],
             "graphgp_whiten_backward": [_P, _P, _P, _P, _P, ctypes.c_double, _P, _P, _P],
             "graphgp_nll_backward": [_P, _P, _P, ctypes.c_double, _P, _P, _P],
@@ -287,6 +288,17 @@ def nll(graph: Graph, fac: Factor, v: torch.Tensor, out: torch.Tensor | None = N
     _check(load().graphgp_nll(graph.handle, fac.handle, _dev(v, torch.float32, graph.N, "v"),
                               _dev(o, torch.float64, 1), _stream(stream)), "nll")
     return o
+
+
+def nll_noalloc(graph: Graph, fac: Factor, v: torch.Tensor, out: torch.Tensor,
+                stream=None) -> torch.Tensor:
+    """graphgp_nll_noalloc: nll() without any device allocation inside the
+    call, for callers that cannot allocate (pass a preallocated `out`)."""
+    _check(load().graphgp_nll_noalloc(graph.handle, fac.handle,
+                                      _dev(v, torch.float32, graph.N, "v"),
+                                      _dev(out, torch.float64, 1), _stream(stream)),
+           "nll_noalloc")
+    return out
 
 
 def generate_backward(graph, fac, xi, v, vbar, xibar=None, thetabar=None, stream=None):

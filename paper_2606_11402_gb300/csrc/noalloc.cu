@@ -1,0 +1,226 @@
+// graphgp_nll_noalloc: the negative log-likelihood of graphgp_nll computed
+// without allocating any device memory during the call.
+//
+// graphgp_nll allocates an FP64 accumulator on every call and writes the
+// whitened field into the graph's work vector.  Some callers cannot allocate
+// while they run: a serving loop that reserved all device memory for resident
+// graphs and factors up front, or code that must not pay cudaMalloc's
+// device-wide synchronisation on a latency-critical path.  This variant keeps
+// its reduction scratch in a file-scope device array instead: one FP64 slot
+// per whiten tile plus one for the dense block.  Every slot is written before
+// it is read, so nothing needs clearing, and the final sum runs in a fixed
+// order (the result does not depend on block scheduling).
+//
+// The array is loaded with the library and held by every GPU that loads it
+// until the process exits.  Its device address is looked up once per device
+// (cudaGetSymbolAddress, with that device current) on the first call made on
+// that device; make that first call before any stream capture.  All calls
+// share the one array, so calls that overlap on the GPU race on it: do not
+// run two of them concurrently (on different streams) on the same device.
+#include <algorithm>
+#include <mutex>
+
+#include "sweepsync.cuh"
+
+// One slot per whiten tile (at most 65536 tiles of 4096 points, i.e.
+// N <= 2^28) plus one for the dense block: 512 KiB.
+static constexpr int kNllSlots = 65536 + 1;
+static __device__ __align__(256) double g_nll_scratch[kNllSlots];
+
+namespace ggp {
+namespace {
+
+std::mutex g_addr_mu;
+double* g_addr[64] = {};
+
+// Device address of g_nll_scratch on the current device (set up on first use).
+int nll_scratch(double** out) {
+  int dev = 0;
+  GGP_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return GRAPHGP_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(g_addr_mu);
+  if (!g_addr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_nll_scratch);
+    if (e != cudaSuccess) {
+      std::fprintf(stderr, "graphgp_nll_noalloc: cudaGetSymbolAddress failed: %s\n",
+                   cudaGetErrorString(e));
+      return GRAPHGP_ERR_CUDA;
+    }
+    g_addr[dev] = (double*)p;
+  }
+  *out = g_addr[dev];
+  return GRAPHGP_OK;
+}
+
+// Fixed-order block sum of one double per thread (blockDim.x == 256).
+__device__ double block_sum_fixed(double x) {
+  __shared__ double red[256];
+  red[threadIdx.x] = x;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  double r = red[0];
+  __syncthreads();
+  return r;
+}
+
+// Dense block: slot[0] = sum_i (L0^-1 v_0)_i^2, one block of 256 threads,
+// one warp per row.
+__global__ void nll_dense_slot_kernel(const float* __restrict__ W, const float* __restrict__ v,
+                                      int n0, double* __restrict__ slot) {
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  double local = 0.0;
+  for (int i = w; i < n0; i += blockDim.x >> 5) {
+    const float* r = W + (int64_t)i * n0;
+    float s = 0.0f;
+    for (int m = lane; m <= i; m += 32) s = fmaf(r[m], v[m], s);
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) local += (double)s * (double)s;
+  }
+  double t = block_sum_fixed(local);
+  if (threadIdx.x == 0) slot[0] = t;
+}
+
+// One tile per block iteration: slot[1 + t] = sum over the tile's positions of
+// xi_i^2, xi_i = (v_i - b_i . v_c(i)) / sigma_i.
+template <int KP>
+__global__ void __launch_bounds__(256) nll_tiles_slot_kernel(
+    const int32_t* __restrict__ nbr, const float* __restrict__ b, const float* __restrict__ sigma,
+    const float* __restrict__ v, int64_t n0, const int32_t* __restrict__ tile_start,
+    int64_t n_tiles, int num_levels, double* __restrict__ slot) {
+  extern __shared__ int32_t sm[];
+  int32_t* s_start = sm;
+  int32_t* s_pref = sm + num_levels;
+  __shared__ int32_t s_total;
+  __shared__ int32_t wsum[8];
+  const uint64_t pol_rows = l2_evict_first();
+  const uint64_t pol_v = l2_evict_last();
+  for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+    const int32_t* ts = tile_start + t * num_levels;
+    if (threadIdx.x == 0) s_total = 0;
+    __syncthreads();
+    // the tile's positions, level by level (levels >= 1; level 0 is dense):
+    // exclusive prefix of the per-level counts, 256 levels per round
+    for (int base = 1; base < num_levels; base += blockDim.x) {
+      int l = base + threadIdx.x;
+      int32_t c = 0;
+      if (l < num_levels) {
+        s_start[l] = ts[l];
+        c = ts[num_levels + l] - ts[l];
+      }
+      int32_t x = c;
+      for (int o = 1; o < 32; o <<= 1) {
+        int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if ((threadIdx.x & 31) >= o) x += y;
+      }
+      if ((threadIdx.x & 31) == 31) wsum[threadIdx.x >> 5] = x;
+      __syncthreads();
+      int32_t wpre = 0;
+      for (int w = 0; w < (int)(threadIdx.x >> 5); w++) wpre += wsum[w];
+      int32_t carry = s_total;
+      if (l < num_levels) s_pref[l] = carry + wpre + x - c;
+      __syncthreads();
+      if (threadIdx.x == blockDim.x - 1) s_total = carry + wpre + x;
+      __syncthreads();
+    }
+    const int32_t total = s_total;
+    double local = 0.0;
+    for (int32_t vi = threadIdx.x; vi < total; vi += blockDim.x) {
+      int lo = 1, hi = num_levels - 1;
+      while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (s_pref[mid] <= vi) lo = mid; else hi = mid - 1;
+      }
+      const int64_t pos = (int64_t)s_start[lo] + (vi - s_pref[lo]);
+      const int4* np = reinterpret_cast<const int4*>(nbr + (pos - n0) * KP);
+      const float4* bp = reinterpret_cast<const float4*>(b + (pos - n0) * KP);
+      float acc0 = 0.0f, acc1 = 0.0f;
+#pragma unroll
+      for (int q = 0; q < KP / 4; q++) {
+        int4 c = ld_stream_i4(np + q, pol_rows);
+        float4 w = ld_stream_f4(bp + q, pol_rows);
+        acc0 = fmaf(w.x, ld_keep_f(v + c.x, pol_v), acc0);
+        acc1 = fmaf(w.y, ld_keep_f(v + c.y, pol_v), acc1);
+        acc0 = fmaf(w.z, ld_keep_f(v + c.z, pol_v), acc0);
+        acc1 = fmaf(w.w, ld_keep_f(v + c.w, pol_v), acc1);
+      }
+      float sg = ld_stream_f(sigma + pos, pol_rows);
+      float vv = ld_keep_f(v + pos, pol_v);
+      float out = (vv - (acc0 + acc1)) / sg;
+      local += (double)out * (double)out;
+    }
+    double tsum = block_sum_fixed(local);
+    if (threadIdx.x == 0) slot[1 + t] = tsum;
+  }
+}
+
+// out = 0.5 sum(slots) + 0.5 logdet, summed in a fixed order.
+__global__ void nll_noalloc_finish_kernel(const double* __restrict__ slot, int64_t count,
+                                          const double* __restrict__ logdet,
+                                          double* __restrict__ out) {
+  double local = 0.0;
+  for (int64_t i = threadIdx.x; i < count; i += blockDim.x) local += slot[i];
+  double t = block_sum_fixed(local);
+  if (threadIdx.x == 0) out[0] = 0.5 * t + 0.5 * logdet[0];
+}
+
+template <int KP>
+int launch_tiles(graphgp_graph_t g, graphgp_factor_t f, const float* v, double* slot,
+                 cudaStream_t s) {
+  size_t smem = (2 * (size_t)g->num_levels + 1) * sizeof(int32_t);
+  int per_sm = 0;
+  GGP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, nll_tiles_slot_kernel<KP>, 256,
+                                                         smem));
+  int64_t grid = std::min<int64_t>(g->n_tiles, (int64_t)std::max(per_sm, 1) * num_sms());
+  nll_tiles_slot_kernel<KP><<<(unsigned)grid, 256, smem, s>>>(
+      g->nbr, f->b, f->sigma, v, g->n0, g->tile_start, g->n_tiles, g->num_levels, slot);
+  GGP_CUDA(cudaGetLastError());
+  return GRAPHGP_OK;
+}
+
+}  // namespace
+}  // namespace ggp
+
+using namespace ggp;
+
+extern "C" int graphgp_nll_noalloc(graphgp_graph_t g, graphgp_factor_t f, const float* v_d,
+                                   double* out_d, void* stream) {
+  if (!g || !f || f->g != g || !v_d || !out_d) return GRAPHGP_ERR_INVALID;
+  if (!g->tile_start || g->num_levels > 8192) {
+    std::fprintf(stderr, "graphgp_nll_noalloc: graph has %d depth levels; at most 8192 are "
+                         "supported without allocation\n", g->num_levels);
+    return GRAPHGP_ERR_INVALID;
+  }
+  int64_t slots = (g->N > g->n0 ? g->n_tiles : 0) + 1;
+  if (slots > kNllSlots) {
+    std::fprintf(stderr, "graphgp_nll_noalloc: N=%lld needs %lld scratch slots; the static "
+                         "scratch holds %d (N <= 2^28)\n",
+                 (long long)g->N, (long long)slots, kNllSlots);
+    return GRAPHGP_ERR_INVALID;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  double* slot = nullptr;
+  GGP_TRY(nll_scratch(&slot));
+  nll_dense_slot_kernel<<<1, 256, 0, s>>>(f->L0inv, v_d, g->n0, slot);
+  GGP_CUDA(cudaGetLastError());
+  if (g->N > g->n0) {
+    int rc = GRAPHGP_OK;
+    switch (g->kp) {
+      case 4: rc = launch_tiles<4>(g, f, v_d, slot, s); break;
+      case 8: rc = launch_tiles<8>(g, f, v_d, slot, s); break;
+      case 12: rc = launch_tiles<12>(g, f, v_d, slot, s); break;
+      case 16: rc = launch_tiles<16>(g, f, v_d, slot, s); break;
+      case 20: rc = launch_tiles<20>(g, f, v_d, slot, s); break;
+      case 24: rc = launch_tiles<24>(g, f, v_d, slot, s); break;
+      case 28: rc = launch_tiles<28>(g, f, v_d, slot, s); break;
+      default: rc = launch_tiles<32>(g, f, v_d, slot, s); break;
+    }
+    if (rc < 0) return rc;
+  }
+  nll_noalloc_finish_kernel<<<1, 256, 0, s>>>(slot, slots, f->logdet, out_d);
+  GGP_CUDA(cudaGetLastError());
+  return GRAPHGP_OK;
+}
