@@ -128,29 +128,51 @@ __global__ void __launch_bounds__(256) nll_tiles_slot_kernel(
     }
     const int32_t total = s_total;
     double local = 0.0;
-    for (int32_t vi = threadIdx.x; vi < total; vi += blockDim.x) {
-      int lo = 1, hi = num_levels - 1;
-      while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (s_pref[mid] <= vi) lo = mid; else hi = mid - 1;
-      }
-      const int64_t pos = (int64_t)s_start[lo] + (vi - s_pref[lo]);
-      const int4* np = reinterpret_cast<const int4*>(nbr + (pos - n0) * KP);
-      const float4* bp = reinterpret_cast<const float4*>(b + (pos - n0) * KP);
-      float acc0 = 0.0f, acc1 = 0.0f;
+    // the same lane split and summation order as the whiten sweep, so the
+    // whitened values are bit-identical to graphgp_nll's
+    constexpr int LANES = KP % 16 == 0 ? 4 : (KP % 8 == 0 ? 2 : 1);
+    constexpr int HP = KP / LANES, GPB = 256 / LANES;
+    const int h = threadIdx.x % LANES;
+    const int32_t steps = (total + GPB - 1) / GPB;
+    for (int32_t st = 0; st < steps; st++) {
+      const int32_t vi = st * GPB + (int32_t)threadIdx.x / LANES;
+      const bool act = vi < total;
+      int64_t pos = 0;
+      float acc = 0.0f;
+      if (act) {
+        int lo = 1, hi = num_levels - 1;
+        while (lo < hi) {
+          int mid = (lo + hi + 1) >> 1;
+          if (s_pref[mid] <= vi) lo = mid; else hi = mid - 1;
+        }
+        pos = (int64_t)s_start[lo] + (vi - s_pref[lo]);
+        const int4* np = reinterpret_cast<const int4*>(nbr + (pos - n0) * KP + h * HP);
+        const float4* bp = reinterpret_cast<const float4*>(b + (pos - n0) * KP + h * HP);
+        int4 c[HP / 4];
+        float4 w[HP / 4];
 #pragma unroll
-      for (int q = 0; q < KP / 4; q++) {
-        int4 c = ld_stream_i4(np + q, pol_rows);
-        float4 w = ld_stream_f4(bp + q, pol_rows);
-        acc0 = fmaf(w.x, ld_keep_f(v + c.x, pol_v), acc0);
-        acc1 = fmaf(w.y, ld_keep_f(v + c.y, pol_v), acc1);
-        acc0 = fmaf(w.z, ld_keep_f(v + c.z, pol_v), acc0);
-        acc1 = fmaf(w.w, ld_keep_f(v + c.w, pol_v), acc1);
+        for (int q = 0; q < HP / 4; q++) {
+          c[q] = ld_stream_i4(np + q, pol_rows);
+          w[q] = ld_stream_f4(bp + q, pol_rows);
+        }
+        float acc0 = 0.0f, acc1 = 0.0f;
+#pragma unroll
+        for (int q = 0; q < HP / 4; q++) {
+          acc0 = fmaf(w[q].x, ld_keep_f(v + c[q].x, pol_v), acc0);
+          acc1 = fmaf(w[q].y, ld_keep_f(v + c[q].y, pol_v), acc1);
+          acc0 = fmaf(w[q].z, ld_keep_f(v + c[q].z, pol_v), acc0);
+          acc1 = fmaf(w[q].w, ld_keep_f(v + c[q].w, pol_v), acc1);
+        }
+        acc = acc0 + acc1;
       }
-      float sg = ld_stream_f(sigma + pos, pol_rows);
-      float vv = ld_keep_f(v + pos, pol_v);
-      float out = (vv - (acc0 + acc1)) / sg;
-      local += (double)out * (double)out;
+      if (LANES >= 4) acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+      if (LANES >= 2) acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+      if (act && h == 0) {
+        float sg = ld_stream_f(sigma + pos, pol_rows);
+        float vv = ld_keep_f(v + pos, pol_v);
+        float out = (vv - acc) / sg;
+        local += (double)out * (double)out;
+      }
     }
     double tsum = block_sum_fixed(local);
     if (threadIdx.x == 0) slot[1 + t] = tsum;

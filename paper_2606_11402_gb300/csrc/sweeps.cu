@@ -84,38 +84,77 @@ __device__ __forceinline__ float gather_dot(const Row<KP>& r, const float* __res
 
 constexpr int kSweepThreads = 256;
 
-template <int KP>
+// lanes per position in generate: row slices of a multiple of 4 entries
+__host__ __device__ constexpr int gen_lanes(int kp) { return kp % 16 == 0 ? 4 : (kp % 8 == 0 ? 2 : 1); }
+
+// LANES threads share one position: lane h holds entries [h HP, (h+1) HP) of
+// the row (HP = KP / LANES) and the partial sums meet in shuffles.  Each lane
+// loads the row of its next position before gathering the current one, so a
+// row load is always in flight under the gathers.
+template <int KP, int LANES>
 __global__ void __launch_bounds__(kSweepThreads) generate_kernel(
     const int32_t* __restrict__ nbr, const float* __restrict__ b, const float* __restrict__ sigma,
     const float* __restrict__ xi, float* v, const int64_t* __restrict__ level_off,
     int num_levels, int64_t n0, LevelBarrier lb) {
+  constexpr int HP = KP / LANES;              // row entries per lane
+  constexpr int GPB = kSweepThreads / LANES;  // lane groups per block
+  constexpr int U = 2;                        // positions per lane group per step
+  constexpr int PPB = U * GPB;                // positions per block step
   __shared__ int s_flag;
   const uint64_t pol_rows = l2_evict_first();
   const uint64_t pol_v = l2_evict_last();
+  const int h = threadIdx.x % LANES;
+  const int slot = threadIdx.x / LANES;
+  const int32_t* nb = nbr + h * HP;
+  const float* bw = b + h * HP;
   for (int l = 1; l < num_levels; l++) {
     // each block takes one contiguous, spatially compact slice of the level
     const int64_t lo = level_off[l], n = level_off[l + 1] - lo;
     const int64_t per = (n + gridDim.x - 1) / gridDim.x;
     const int64_t b0 = lo + min((int64_t)blockIdx.x * per, n);
     const int64_t hi = lo + min((int64_t)(blockIdx.x + 1) * per, n);
-    int64_t p = b0 + threadIdx.x;
-    Row<KP> r;
-    float sg = 0.0f, x = 0.0f;
-    if (p < hi) {
-      load_row<KP>(r, nbr, b, p - n0, pol_rows);
-      sg = ld_stream_f(sigma + p, pol_rows);
-      x = ld_stream_f(xi + p, pol_rows);
+    int64_t p = b0 + slot;  // positions p + u GPB, u < U
+    Row<HP> r[U];
+    float sg[U], x[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      const int64_t q = p + u * GPB;
+      sg[u] = x[u] = 0.0f;
+      if (q < hi) {
+        load_row<HP>(r[u], nb, bw, (q - n0) * LANES, pol_rows);
+        if (h == 0) {
+          sg[u] = ld_stream_f(sigma + q, pol_rows);
+          x[u] = ld_stream_f(xi + q, pol_rows);
+        }
+      }
     }
     if (l > 1 && lb.wait(l - 1, gridDim.x, &s_flag)) return;
-    while (p < hi) {
-      float acc = gather_dot<KP, true>(r, v, pol_v);
-      st_keep_f(v + p, fmaf(sg, x, acc), pol_v);
-      p += blockDim.x;
-      if (p < hi) {
-        load_row<KP>(r, nbr, b, p - n0, pol_rows);
-        sg = ld_stream_f(sigma + p, pol_rows);
-        x = ld_stream_f(xi + p, pol_rows);
+    // every lane of a warp runs the same number of steps (shuffles below)
+    const int64_t steps = (hi - b0 + PPB - 1) / PPB;
+    for (int64_t st = 0; st < steps; st++) {
+      float acc[U];
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        const int64_t q = p + u * GPB;
+        acc[u] = q < hi ? gather_dot<HP, true>(r[u], v, pol_v) : 0.0f;
       }
+      const int64_t pn = p + PPB;
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        if (LANES >= 4) acc[u] += __shfl_xor_sync(0xffffffffu, acc[u], 2);
+        if (LANES >= 2) acc[u] += __shfl_xor_sync(0xffffffffu, acc[u], 1);
+        const int64_t q = p + u * GPB;
+        if (q < hi && h == 0) st_keep_f(v + q, fmaf(sg[u], x[u], acc[u]), pol_v);
+        const int64_t qn = pn + u * GPB;
+        if (qn < hi) {
+          load_row<HP>(r[u], nb, bw, (qn - n0) * LANES, pol_rows);
+          if (h == 0) {
+            sg[u] = ld_stream_f(sigma + qn, pol_rows);
+            x[u] = ld_stream_f(xi + qn, pol_rows);
+          }
+        }
+      }
+      p = pn;
     }
     __syncthreads();
     lb.arrive(l);
@@ -127,7 +166,7 @@ __global__ void __launch_bounds__(256) whiten_kernel(
     const int32_t* __restrict__ nbr, const float* __restrict__ b, const float* __restrict__ sigma,
     const float* __restrict__ v, float* __restrict__ xi, int64_t N, int64_t n0,
     double* __restrict__ sq) {
-  const uint64_t pol_rows = l2_evict_first();
+  const uint64_t pol_rows = l2_policy<0>();  // whiten: rows evict-normal (measured best)
   const uint64_t pol_v = l2_evict_last();
   double local = 0.0;
   for (int64_t pos = n0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; pos < N;
@@ -167,7 +206,7 @@ __global__ void __launch_bounds__(256) whiten_tiles_kernel(
   int32_t* s_start = sm;               // [num_levels]
   int32_t* s_pref = sm + num_levels;   // [num_levels + 1]
   __shared__ int32_t s_carry;
-  const uint64_t pol_rows = l2_evict_first();
+  const uint64_t pol_rows = l2_policy<0>();  // whiten: rows evict-normal (measured best)
   const uint64_t pol_v = l2_evict_last();
   double local = 0.0;
   for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
@@ -201,22 +240,37 @@ __global__ void __launch_bounds__(256) whiten_tiles_kernel(
       __syncthreads();
     }
     const int32_t total = s_carry;
-    for (int32_t vi = threadIdx.x; vi < total; vi += blockDim.x) {
-      // level of vi: last l >= 1 with s_pref[l] <= vi
-      int lo = 1, hi = num_levels - 1;
-      while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (s_pref[mid] <= vi) lo = mid; else hi = mid - 1;
+    // LANES lanes share a position; lane h holds row entries [h HP, (h+1) HP),
+    // so a warp reads 32/LANES consecutive rows as whole sectors
+    constexpr int LANES = gen_lanes(KP), HP = KP / LANES, GPB = 256 / LANES;
+    const int h = threadIdx.x % LANES;
+    const int32_t steps = (total + GPB - 1) / GPB;
+    for (int32_t st = 0; st < steps; st++) {
+      const int32_t vi = st * GPB + (int32_t)threadIdx.x / LANES;
+      const bool act = vi < total;
+      int64_t pos = 0;
+      float acc = 0.0f;
+      if (act) {
+        // level of vi: last l >= 1 with s_pref[l] <= vi
+        int lo = 1, hi = num_levels - 1;
+        while (lo < hi) {
+          int mid = (lo + hi + 1) >> 1;
+          if (s_pref[mid] <= vi) lo = mid; else hi = mid - 1;
+        }
+        pos = (int64_t)s_start[lo] + (vi - s_pref[lo]);
+        Row<HP> r;
+        load_row<HP>(r, nbr + h * HP, b + h * HP, (pos - n0) * LANES, pol_rows);
+        acc = gather_dot<HP, false>(r, v, pol_v);
       }
-      const int64_t pos = (int64_t)s_start[lo] + (vi - s_pref[lo]);
-      Row<KP> r;
-      load_row<KP>(r, nbr, b, pos - n0, pol_rows);
-      float sg = ld_stream_f(sigma + pos, pol_rows);
-      float vv = ld_keep_f(v + pos, pol_v);
-      float acc = gather_dot<KP, false>(r, v, pol_v);
-      float out = (vv - acc) / sg;
-      st_stream_f(xi + pos, out, pol_rows);
-      if (sq) local += (double)out * (double)out;
+      if (LANES >= 4) acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+      if (LANES >= 2) acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+      if (act && h == 0) {
+        float sg = ld_stream_f(sigma + pos, pol_rows);
+        float vv = ld_keep_f(v + pos, pol_v);
+        float out = (vv - acc) / sg;
+        st_stream_f(xi + pos, out, pol_rows);
+        if (sq) local += (double)out * (double)out;
+      }
     }
     __syncthreads();
   }
@@ -244,7 +298,7 @@ int launch_generate(graphgp_graph_t g, graphgp_factor_t f, const float* xi, floa
   if (g->num_levels <= 1) return GRAPHGP_OK;
   GGP_CUDA(cudaMemsetAsync(g->level_bar, 0, g->num_levels * sizeof(uint32_t), s));
   static int max_grid = 0;
-  if (!max_grid) max_grid = coop_grid(generate_kernel<KP>, kSweepThreads);
+  if (!max_grid) max_grid = coop_grid(generate_kernel<KP, gen_lanes(KP)>, kSweepThreads);
   int64_t want = (g->max_level_size + kSweepThreads - 1) / kSweepThreads;
   int grid = (int)std::min<int64_t>(max_grid, std::max<int64_t>(want, 1));
   LevelBarrier lb{g->level_bar, g->err, g->max_spin};
@@ -256,7 +310,7 @@ int launch_generate(graphgp_graph_t g, graphgp_factor_t f, const float* xi, floa
   int64_t n0 = g->n0;
   void* args[] = {(void*)&nbr, (void*)&bw, (void*)&sg, (void*)&xi, (void*)&v,
                   (void*)&lo,  (void*)&nl, (void*)&n0, (void*)&lb};
-  GGP_CUDA(cudaLaunchCooperativeKernel((const void*)generate_kernel<KP>, dim3(grid),
+  GGP_CUDA(cudaLaunchCooperativeKernel((const void*)generate_kernel<KP, gen_lanes(KP)>, dim3(grid),
                                        dim3(kSweepThreads), args, 0, s));
   return GRAPHGP_OK;
 }
