@@ -111,6 +111,60 @@ def cpu_baseline(N_sample=1 << 18, reps=10):
             "graph_points_per_s": N_sample / t_graph, "factor_points_per_s": N_sample / t_factor}
 
 
+def serving_bench(n_inst=64, rate=2000.0, duration=5.0, seed=8, n_slots=8):
+    """Poisson stream of generate / whiten / logdet / NLL-gradient requests over
+    a pool of resident instances: N log-uniform in [1e3, 1e6], k in {8, 16, 32},
+    Matern-3/2 with l log-uniform in [0.01, 0.2], half uniform and half
+    clustered clouds.  Returns the engine's and the one-at-a-time form's
+    p50/p99 latency and throughput on the same arrivals."""
+    import numpy as np
+    import torch
+
+    import paper_2606_11402_gb300 as gg
+    import workloads
+    from paper_2606_11402_gb300 import serve as sv
+    rng = np.random.Generator(np.random.PCG64(seed))
+    inst, inputs, total_pts = [], [], 0
+    t0 = time.perf_counter()
+    for i in range(n_inst):
+        N = int(10 ** rng.uniform(3.0, 6.0))
+        k = int(rng.choice([8, 16, 32]))
+        ell = float(10 ** rng.uniform(-2.0, np.log10(0.2)))
+        pts = (workloads.uniform_cube(N, seed * 1000 + i) if i % 2 == 0 else
+               workloads.blobs(N, seed * 1000 + i, n_blobs=100))
+        g = gg.build_graph(torch.from_numpy(pts).cuda(), k, n0=min(N, 256))
+        f = gg.factor(g, gg.Kernel(gg.MATERN32, 1.0, ell, 1e-6))
+        inst.append((g, f))
+        inputs.append(torch.from_numpy(workloads.white_noise(N, seed * 1000 + i)).pin_memory())
+        total_pts += N
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t0
+    reqs = sv.poisson_stream(n_inst, rate, duration, seed + 1)
+    warm = sv.poisson_stream(n_inst, rate, 0.5, seed + 2)
+    server = sv.Server(n_slots=n_slots)
+    for g, f in inst:
+        server.register(g, f)
+    server.start()
+    # capture every (instance, op, slot) graph before timing
+    for _ in range(n_slots):
+        tks = [server.submit(i, op, inputs[i]) for i in range(n_inst) for op in sv.OPS]
+        for t in tks:
+            server.wait(t)
+    sv.run_stream(warm, inputs, server=server)
+    eng = sv.run_stream(reqs, inputs, server=server)
+    server.close()
+    sv.run_stream(warm, inputs, instances=inst)
+    one = sv.run_stream(reqs, inputs, instances=inst)
+    pts_req = float(np.mean([inst[r.inst][0].N for r in reqs])) if reqs else 0.0
+    return {"workload": (f"Poisson {rate:.0f} req/s for {duration:.0f} s over {n_inst} resident "
+                         "instances (N log-uniform 1e3..1e6, k in {8,16,32}, Matern-3/2 "
+                         "l log-uniform 0.01..0.2, uniform/clustered), ops uniform over "
+                         "generate/whiten/logdet/nll-gradient"),
+            "engine": eng, "one_at_a_time": one, "slots": n_slots,
+            "mean_points_per_request": pts_req, "setup_s": t_setup,
+            "instances_points": total_pts}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -280,6 +334,11 @@ def run_ours(args):
         "gpu_launches": 4 * args.steps,
         "clocks": _clock_summary(os.path.join("/tmp", f"ggp_clocks_{rank}.csv"), local),
     }
+    if rank == 0 and not args.no_serve:
+        sb = serving_bench(duration=args.serve_duration)
+        line["serving"] = sb
+        line["serving_p50_ms"] = sb["engine"]["p50_ms"]
+        line["serving_p99_ms"] = sb["engine"]["p99_ms"]
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = {kk: vv for kk, vv in cpu_baseline().items()
                                 if kk in ("value", "unit", "cores", "kind", "sample")}
@@ -299,6 +358,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--N", type=int, default=0, help="override N (profiling a smaller case)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving stream")
+    ap.add_argument("--serve-duration", type=float, default=5.0)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -210,6 +210,51 @@ int graphgp_nll_backward(graphgp_graph_t g, graphgp_factor_t f,
                          const float* v_d, double nllbar, float* vbar_d,
                          double* thetabar_d, void* stream);
 
+/* ---- serving (continuous batching over resident instances) -------------
+ * Not a paper algorithm: an engine that serves the operations above, each
+ * request on one resident instance (a graph with its factor).  A native
+ * scheduler thread admits queued requests in arrival order while a stream
+ * slot is free and the device bytes of the requests in flight stay within
+ * hbm_budget (0 = 8 GiB); requests on different slots overlap on the device.
+ * One request per instance runs at a time.  With use_graphs, the first
+ * request of each (instance, operation, slot) is captured into a CUDA graph
+ * that later requests replay.
+ *   op GENERATE: in_h = xi[N] -> out_h = v[N]
+ *   op WHITEN:   in_h = v[N]  -> out_h = xi[N]
+ *   op LOGDET:   scal_h[0] = logdet
+ *   op NLL_GRAD: in_h = v[N]  -> out_h = dNLL/dv[N], scal_h[0] = NLL,
+ *                scal_h[1..3] = dNLL/d(lengthscale, sigma2, nugget)
+ * in_h/out_h are host buffers (pinned for asynchronous copies); out_h and
+ * scal_h may be NULL (results land in the slot's staging buffers).  The
+ * caller keeps every buffer alive until the request completes.  Instances
+ * must stay alive until graphgp_server_destroy, and must not be used by
+ * other calls while the server runs. */
+typedef struct graphgp_server_s* graphgp_server_t;
+enum { GRAPHGP_OP_GENERATE = 0, GRAPHGP_OP_WHITEN = 1, GRAPHGP_OP_LOGDET = 2,
+       GRAPHGP_OP_NLL_GRAD = 3 };
+
+int graphgp_server_create(int n_slots, size_t hbm_budget, int use_graphs,
+                          graphgp_server_t* out);
+/* Before graphgp_server_start only.  Builds the instance's children CSR
+ * (synchronises the device). */
+int graphgp_server_register(graphgp_server_t sv, graphgp_graph_t g,
+                            graphgp_factor_t f, int* instance_id);
+int graphgp_server_start(graphgp_server_t sv);
+/* arrival_s: the request's arrival time on the host monotonic clock
+ * (CLOCK_MONOTONIC seconds; <= 0 means now).  Writes a ticket. */
+int graphgp_server_submit(graphgp_server_t sv, int instance_id, int op,
+                          const float* in_h, float* out_h, double* scal_h,
+                          double arrival_s, uint64_t* ticket);
+/* Waits up to timeout_s for a ticket; returns its status (GRAPHGP_ERR_TIMEOUT
+ * if still running).  times_out (nullable) = [arrival, admit, done]. */
+int graphgp_server_wait(graphgp_server_t sv, uint64_t ticket, double timeout_s,
+                        double* times_out);
+int graphgp_server_stats(graphgp_server_t sv, int64_t* completed, int64_t* errors,
+                         int64_t* queued, size_t* bytes_in_flight);
+/* Drains the queue, joins the scheduler and frees the server (not the
+ * instances). */
+void graphgp_server_destroy(graphgp_server_t sv);
+
 const char* graphgp_status_string(int status);
 
 #ifdef __cplusplus

@@ -107,6 +107,13 @@ def load() -> ctypes.CDLL:
     return _lib
 
 
+def lib() -> ctypes.CDLL:
+    """The loaded library (alias of load())."""
+    if _lib is None:
+        load()
+    return _lib
+
+
 def status_string(status: int) -> str:
     return load().graphgp_status_string(status).decode()
 

@@ -1,0 +1,113 @@
+"""Differentiable GraphGP operations (torch.autograd.Function over the C ABI).
+
+theta is a float64 tensor [lengthscale, sigma2, nugget] of the stationary
+covariance of Sec. 2.1; gradients with respect to it come from the library's
+adjoint kernels (Sec. 2.3: derivatives through the Cholesky factors, which are
+recomputed rather than stored).  Vectors are float32 CUDA tensors in graph
+order.  Every function builds the factor for the given theta (one
+graphgp_factor call) unless a Factor is passed in.
+
+    v   = generate(graph, kernel_type, theta, xi)      # v = L xi
+    xi  = whiten(graph, kernel_type, theta, v)         # xi = L^-1 v
+    ld  = logdet(graph, kernel_type, theta)            # log det L L^T
+    nll = nll(graph, kernel_type, theta, v)            # 0.5 xi.xi + 0.5 ld
+"""
+from __future__ import annotations
+
+import torch
+
+from . import (Factor, Graph, Kernel, factor as _factor, generate_backward, logdet as _logdet,
+               nll as _nll, nll_backward, whiten_backward, generate as _generate,
+               whiten as _whiten)
+
+
+def _kernel(kernel_type: int, theta: torch.Tensor) -> Kernel:
+    t = theta.detach().double().cpu()
+    return Kernel(int(kernel_type), float(t[1]), float(t[0]), float(t[2]))
+
+
+def _theta_grad(tb: torch.Tensor, theta: torch.Tensor) -> torch.Tensor:
+    return tb.to(device=theta.device, dtype=theta.dtype)
+
+
+class _Generate(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, xi, theta, graph, kernel_type):
+        f = _factor(graph, _kernel(kernel_type, theta))
+        v = _generate(graph, f, xi.contiguous())
+        ctx.graph, ctx.fac = graph, f
+        ctx.save_for_backward(xi, v, theta)
+        return v
+
+    @staticmethod
+    def backward(ctx, grad_v):
+        xi, v, theta = ctx.saved_tensors
+        xibar, tb = generate_backward(ctx.graph, ctx.fac, xi.contiguous(), v,
+                                      grad_v.contiguous().float())
+        return xibar, _theta_grad(tb, theta), None, None
+
+
+class _Whiten(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, v, theta, graph, kernel_type):
+        f = _factor(graph, _kernel(kernel_type, theta))
+        xi = _whiten(graph, f, v.contiguous())
+        ctx.graph, ctx.fac = graph, f
+        ctx.save_for_backward(v, xi, theta)
+        return xi
+
+    @staticmethod
+    def backward(ctx, grad_xi):
+        v, xi, theta = ctx.saved_tensors
+        vbar, tb = whiten_backward(ctx.graph, ctx.fac, v.contiguous(), xi,
+                                   grad_xi.contiguous().float(), 0.0)
+        return vbar, _theta_grad(tb, theta), None, None
+
+
+class _Logdet(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, theta, graph, kernel_type):
+        f = _factor(graph, _kernel(kernel_type, theta))
+        ctx.graph, ctx.fac = graph, f
+        ctx.save_for_backward(theta)
+        return _logdet(f).reshape(())
+
+    @staticmethod
+    def backward(ctx, grad):
+        (theta,) = ctx.saved_tensors
+        g = ctx.graph
+        z = torch.zeros(g.N, dtype=torch.float32, device="cuda")
+        _, tb = whiten_backward(g, ctx.fac, z, z, z, float(grad.item()))
+        return _theta_grad(tb, theta), None, None
+
+
+class _Nll(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, v, theta, graph, kernel_type):
+        f = _factor(graph, _kernel(kernel_type, theta))
+        out = _nll(graph, f, v.contiguous()).reshape(())
+        ctx.graph, ctx.fac = graph, f
+        ctx.save_for_backward(v, theta)
+        return out
+
+    @staticmethod
+    def backward(ctx, grad):
+        v, theta = ctx.saved_tensors
+        vbar, tb = nll_backward(ctx.graph, ctx.fac, v.contiguous(), float(grad.item()))
+        return vbar, _theta_grad(tb, theta), None, None
+
+
+def generate(graph: Graph, kernel_type: int, theta: torch.Tensor, xi: torch.Tensor):
+    return _Generate.apply(xi, theta, graph, kernel_type)
+
+
+def whiten(graph: Graph, kernel_type: int, theta: torch.Tensor, v: torch.Tensor):
+    return _Whiten.apply(v, theta, graph, kernel_type)
+
+
+def logdet(graph: Graph, kernel_type: int, theta: torch.Tensor):
+    return _Logdet.apply(theta, graph, kernel_type)
+
+
+def nll(graph: Graph, kernel_type: int, theta: torch.Tensor, v: torch.Tensor):
+    return _Nll.apply(v, theta, graph, kernel_type)

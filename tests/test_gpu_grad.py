@@ -128,3 +128,42 @@ def test_ill_conditioned_kernel_error_scales_with_condition(gpu_lib):
     vbar, tb = gpu_lib.nll_backward(g, f, to_gpu(v))
     assert rel_norm(np_(vbar), vbar_or) < tol, (cond, tol)
     assert np.all(np.abs(np_(tb) - tb_or) <= max(2e-3, tol * 10) * np.abs(tb_or).max())
+
+
+def test_autograd_functions_match_oracle(gpu_lib):
+    """torch.autograd over the C-ABI adjoints: d NLL / d(v, theta) and the
+    chain generate -> whiten against the oracle's closed forms."""
+    from paper_2606_11402_gb300 import autograd as ga
+    kind, N, k, kern = CASES[0]
+    g, f, want, fo, K = _setup(gpu_lib, kind, N, k, kern)
+    theta = torch.tensor([kern[2], kern[1], kern[3]], dtype=torch.float64, requires_grad=True)
+    v = oracle.generate(fo, want["nbr_pos"], k, 64,
+                        workloads.white_noise(N, 71).astype(np.float64)).astype(np.float32)
+    vt = to_gpu(v).requires_grad_(True)
+    loss = ga.nll(g, kern[0], theta, vt)
+    loss.backward()
+    vbar_or, tb_or = oracle.nll_grad(want, K, v.astype(np.float64))
+    assert rel_norm(np_(vt.grad), vbar_or) < 1e-4
+    _theta_close(theta.grad.numpy(), tb_or)
+    # generate then a linear functional: d/dxi = L^T w, d/dtheta vs oracle
+    xi = workloads.white_noise(N, 72)
+    w = np.random.default_rng(5).standard_normal(N).astype(np.float32)
+    theta2 = theta.detach().clone().requires_grad_(True)
+    xit = to_gpu(xi).requires_grad_(True)
+    out = ga.generate(g, kern[0], theta2, xit)
+    (out * to_gpu(w)).sum().backward()
+    a = oracle.generate_vjp(fo, want["nbr_pos"], k, 64, xi.astype(np.float64),
+                            oracle.generate(fo, want["nbr_pos"], k, 64, xi.astype(np.float64)),
+                            w.astype(np.float64))
+    tb2 = oracle.factor_backward(want["pts_pos"], want["nbr_pos"], k, 64, K, a["bbar"], a["bdbar"],
+                                 a["sigbar"])
+    assert rel_norm(np_(xit.grad), a["xibar"]) < 1e-4
+    _theta_close(theta2.grad.numpy(), tb2)
+    # logdet alone
+    theta3 = theta.detach().clone().requires_grad_(True)
+    ga.logdet(g, kern[0], theta3).backward()
+    z = np.zeros(N)
+    a3 = oracle.whiten_vjp(fo, want["nbr_pos"], k, 64, z, z, z, 1.0)
+    tb3 = oracle.factor_backward(want["pts_pos"], want["nbr_pos"], k, 64, K, a3["bbar"],
+                                 a3["bdbar"], a3["sigbar"])
+    _theta_close(theta3.grad.numpy(), tb3)
