@@ -47,6 +47,36 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+def _measured_traffic(kernel: str, N: int):
+    """DRAM bytes per launch of `kernel` from profiles/sweeps_traffic_N2e26.txt,
+    or None when the capture does not cover this N or the kernel sources have
+    changed since it was taken (sha256 recorded in the file)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "sweeps_traffic_N2e26.txt")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    want, n_cap, traffic = {}, None, None
+    for line in text.splitlines():
+        if line.startswith("source_sha256 "):
+            f, h = line[len("source_sha256 "):].split(":")
+            want[f.strip()] = h.strip()
+        elif line.startswith("N:"):
+            n_cap = int(line.split(":")[1])
+        elif line.startswith(kernel + ":"):
+            for kv in line.split()[1:]:
+                if kv.startswith("traffic_bytes="):
+                    traffic = int(kv.split("=")[1])
+    if n_cap != N or traffic is None or not want:
+        return None
+    for f, h in want.items():
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            if hashlib.sha256(fh.read()).hexdigest() != h:
+                return None
+    return traffic
+
+
 def _clock_sampler(out_path):
     q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -318,7 +348,9 @@ def run_ours(args):
                    "l2": "inputs larger than L2 (no flush)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm,
-                     "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                     "unit": "GB/s", "frac": achieved / hbm,
+                     "traffic": _measured_traffic(
+                         "generate_kernel" if dom == "generate" else "whiten_tiles_kernel", N),
                      "peak_kind": peak_kind,
                      "bytes_per_point": bytes_per_point, "points_per_launch": rows},
         "stages": {"generate_ms": gen_ms, "whiten_ms": wh_ms,

@@ -298,20 +298,26 @@ extern "C" int graphgp_build_graph(const float* points_d, int64_t N, int d, int 
     GGP_CUDA(cudaMemsetAsync(g->depth_tree, 0, N * sizeof(int32_t), s));
     unsigned long long* minc = nullptr;
     GGP_TRY(sc.alloc(&minc, 1));
-    int64_t first = n0;
+    // One k-d tree level at a time: a node's neighbours lie in its own or an
+    // earlier tree level, so once the earlier levels are final a level needs
+    // only as many passes as its own longest internal chain.
     int64_t passes = 0;
-    while (first < N) {
-      const unsigned long long none = ~0ull;
-      GGP_CUDA(cudaMemcpyAsync(minc, &none, 8, cudaMemcpyHostToDevice, s));
-      depth_pass_kernel<<<grid_for(N - first, 256, 16), 256, 0, s>>>(g->nbr_tree, g->depth_tree,
-                                                                      N, k, n0, first, minc);
-      GGP_CUDA(cudaGetLastError());
-      unsigned long long mc = 0;
-      GGP_CUDA(cudaMemcpyAsync(&mc, minc, 8, cudaMemcpyDeviceToHost, s));
-      GGP_CUDA(cudaStreamSynchronize(s));
-      if (mc == none) break;
-      first = (int64_t)mc;
-      if (++passes > N) return GRAPHGP_ERR_TIMEOUT;
+    for (int t = 0; ((int64_t(1) << t) - 1) < N; t++) {
+      int64_t first = std::max<int64_t>(n0, (int64_t(1) << t) - 1);
+      const int64_t end = std::min<int64_t>(N, (int64_t(2) << t) - 1);
+      while (first < end) {
+        const unsigned long long none = ~0ull;
+        GGP_CUDA(cudaMemcpyAsync(minc, &none, 8, cudaMemcpyHostToDevice, s));
+        depth_pass_kernel<<<grid_for(end - first, 256, 16), 256, 0, s>>>(
+            g->nbr_tree, g->depth_tree, end, k, n0, first, minc);
+        GGP_CUDA(cudaGetLastError());
+        unsigned long long mc = 0;
+        GGP_CUDA(cudaMemcpyAsync(&mc, minc, 8, cudaMemcpyDeviceToHost, s));
+        GGP_CUDA(cudaStreamSynchronize(s));
+        if (mc == none) break;
+        first = (int64_t)mc;
+        if (++passes > N) return GRAPHGP_ERR_TIMEOUT;
+      }
     }
     int* dmax = nullptr;
     GGP_TRY(sc.alloc(&dmax, 1));
