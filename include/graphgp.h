@@ -255,6 +255,13 @@ int graphgp_server_stats(graphgp_server_t sv, int64_t* completed, int64_t* error
  * instances). */
 void graphgp_server_destroy(graphgp_server_t sv);
 
+/* Self-test of the bounded device waits of the level sweeps (not a paper
+ * operation): a small cooperative launch waits at a level barrier that no
+ * block ever reaches, giving up after max_spin polls (1 <= max_spin <= 2^30).
+ * Synchronises `stream`.  Returns GRAPHGP_ERR_TIMEOUT when the waits gave up
+ * and recorded the timeout as designed (the context stays usable). */
+int graphgp_selftest_wait_timeout(int64_t max_spin, void* stream);
+
 const char* graphgp_status_string(int status);
 
 #ifdef __cplusplus

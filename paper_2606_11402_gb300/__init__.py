@@ -92,6 +92,7 @@ def load() -> ctypes.CDLL:
             "graphgp_generate_backward": [_P, _P, _P, _P, _P, _P, _P, _P],
             "graphgp_whiten_backward": [_P, _P, _P, _P, _P, ctypes.c_double, _P, _P, _P],
             "graphgp_nll_backward": [_P, _P, _P, ctypes.c_double, _P, _P, _P],
+            "graphgp_selftest_wait_timeout": [_I64, _P],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -295,6 +296,12 @@ def nll(graph: Graph, fac: Factor, v: torch.Tensor, out: torch.Tensor | None = N
     _check(load().graphgp_nll(graph.handle, fac.handle, _dev(v, torch.float32, graph.N, "v"),
                               _dev(o, torch.float64, 1), _stream(stream)), "nll")
     return o
+
+
+def selftest_wait_timeout(max_spin: int = 20000, stream=None) -> int:
+    """Runs the bounded-wait self-test; returns its status (ERR_TIMEOUT when the
+    device waits gave up as designed)."""
+    return load().graphgp_selftest_wait_timeout(int(max_spin), _stream(stream))
 
 
 def nll_noalloc(graph: Graph, fac: Factor, v: torch.Tensor, out: torch.Tensor,

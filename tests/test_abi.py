@@ -58,3 +58,31 @@ def test_binding_refuses_missing_library(monkeypatch, tmp_path):
     monkeypatch.setattr(gg, "_lib", None)
     with pytest.raises(ImportError):
         gg.load()
+
+
+def test_host_side_argument_errors_without_gpu(libpath):
+    """Arguments are validated on the host before any CUDA call."""
+    import numpy as np
+    lib = ctypes.CDLL(libpath)
+    out = ctypes.c_void_p()
+    lib.graphgp_build_graph.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    assert lib.graphgp_build_graph(None, 100, 3, 8, None, None, ctypes.byref(out)) == -1
+    assert lib.graphgp_selftest_wait_timeout(ctypes.c_int64(0), None) == -1
+    # graph import: order must be a permutation and neighbours must precede
+    lib.graphgp_graph_import.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+    N, k, n0 = 6, 1, 2
+    pts = np.zeros((N, 3), np.float32)
+    lo = np.array([0, 2, 4, 6], np.int64)
+    nbr = np.array([0, 1, 2, 3], np.int32)
+    bad_order = np.array([0, 1, 2, 3, 4, 4], np.int32)
+    assert lib.graphgp_graph_import(pts.ctypes.data, N, k, n0, bad_order.ctypes.data,
+                                    nbr.ctypes.data, lo.ctypes.data, 3, None,
+                                    ctypes.byref(out)) == -1
+    order = np.arange(N, dtype=np.int32)
+    late = np.array([0, 2, 3, 3], np.int32)  # position 3 conditions on 2, same level
+    assert lib.graphgp_graph_import(pts.ctypes.data, N, k, n0, order.ctypes.data,
+                                    late.ctypes.data, lo.ctypes.data, 3, None,
+                                    ctypes.byref(out)) == -1
