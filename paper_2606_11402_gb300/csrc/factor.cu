@@ -87,6 +87,46 @@ __global__ void __launch_bounds__(128) point_factor_kernel(
   if (lane == 0 && clamped_rows) atomicAdd(not_pd, clamped_rows);
 }
 
+// One thread per point for k <= 16 (K = padded row length): the neighbour row
+// arrives as int4 loads, the k + 1 coordinates as float4 gathers, and the
+// whole factor stays in registers (point_factor_thread).  Same values as the
+// group kernel, bit for bit.
+template <int K, int KT>
+__global__ void __launch_bounds__(128) point_factor_thread_kernel(
+    const float4* __restrict__ xs, const int32_t* __restrict__ nbr, int64_t N, int k, int64_t n0,
+    KernF kf, float* __restrict__ b_out, float* __restrict__ sigma_out,
+    double* __restrict__ logdet, unsigned long long* __restrict__ not_pd) {
+  LogAcc acc;
+  unsigned long long clamped_rows = 0;
+  const int64_t npts = N - n0;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < npts;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = n0 + t;
+    const int4* row = reinterpret_cast<const int4*>(nbr + t * K);
+    float4 x[K];
+#pragma unroll
+    for (int q = 0; q < K / 4; q++) {
+      const int4 c = __ldg(row + q);
+      x[4 * q] = __ldg(xs + c.x);
+      x[4 * q + 1] = __ldg(xs + c.y);
+      x[4 * q + 2] = __ldg(xs + c.z);
+      x[4 * q + 3] = __ldg(xs + c.w);
+    }
+    PointRegs<K> p;
+    point_factor_thread<K, KT>(p, k, kf, x, __ldg(xs + i));
+    float4* bo = reinterpret_cast<float4*>(b_out + t * K);
+#pragma unroll
+    for (int q = 0; q < K / 4; q++)
+      bo[q] = make_float4(p.y[4 * q], p.y[4 * q + 1], p.y[4 * q + 2], p.y[4 * q + 3]);
+    sigma_out[i] = p.sigma;
+    acc.mul(p.sigma);
+    if (p.clamped) clamped_rows++;
+  }
+  block_add_double(acc.log_value(), logdet);
+  for (int o = 16; o; o >>= 1) clamped_rows += __shfl_xor_sync(0xffffffffu, clamped_rows, o);
+  if ((threadIdx.x & 31) == 0 && clamped_rows) atomicAdd(not_pd, clamped_rows);
+}
+
 // Dense block: K_00 (lower triangle) in global memory.
 template <int KT>
 __global__ void dense_fill_kernel(const float4* __restrict__ xs, int n0, KernF kf,
@@ -189,14 +229,37 @@ int launch_point(int type, graphgp_graph_t g, graphgp_factor_t f, const KernF& k
   return GRAPHGP_OK;
 }
 
+template <int K>
+int launch_point_thread(int type, graphgp_graph_t g, graphgp_factor_t f, const KernF& kf,
+                        cudaStream_t s) {
+  const int64_t npts = g->N - g->n0;
+  const unsigned grid = grid_for(npts, 128, 8);
+#define GGP_PT(KT)                                                                       \
+  point_factor_thread_kernel<K, KT><<<grid, 128, 0, s>>>(g->xs, g->nbr, g->N, g->k, g->n0, kf, \
+                                                         f->b, f->sigma, f->logdet, f->not_pd)
+  switch (type) {
+    case GRAPHGP_MATERN12: GGP_PT(GRAPHGP_MATERN12); break;
+    case GRAPHGP_MATERN32: GGP_PT(GRAPHGP_MATERN32); break;
+    case GRAPHGP_MATERN52: GGP_PT(GRAPHGP_MATERN52); break;
+    default: GGP_PT(GRAPHGP_SQEXP); break;
+  }
+#undef GGP_PT
+  GGP_CUDA(cudaGetLastError());
+  return GRAPHGP_OK;
+}
+
 }  // namespace
 
 int point_factor(graphgp_graph_t g, graphgp_factor_t f, const KernF& kf, int type,
                  cudaStream_t s) {
   if (g->N <= g->n0) return GRAPHGP_OK;
-  if (g->k <= 8) return launch_point<8>(type, g, f, kf, s);
-  if (g->k <= 16) return launch_point<16>(type, g, f, kf, s);
-  return launch_point<32>(type, g, f, kf, s);
+  switch (g->kp) {
+    case 4: return launch_point_thread<4>(type, g, f, kf, s);
+    case 8: return launch_point_thread<8>(type, g, f, kf, s);
+    case 12: return launch_point_thread<12>(type, g, f, kf, s);
+    case 16: return launch_point_thread<16>(type, g, f, kf, s);
+    default: return launch_point<32>(type, g, f, kf, s);
+  }
 }
 
 int dense_factor(graphgp_graph_t g, graphgp_factor_t f, const KernF& kf, int type,

@@ -13,6 +13,8 @@
 // its diagonal entry is raised to that floor and flagged.
 #pragma once
 
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace ggp {
@@ -157,6 +159,129 @@ __device__ __forceinline__ float group_chol_solve(const PointState<G>& st, int a
     if (a < j) d = fmaf(-Lg[j * SG + a], gj, d);
   }
   return g_own;
+}
+
+
+
+// ---- one thread per point (k <= 16) ----------------------------------------
+// The same arithmetic as point_factor_group, element by element and in the
+// same order, but with the whole lower triangle of L in one thread's
+// registers: no shuffles, no shared memory, each kernel value evaluated once
+// (the group form evaluates every row in full on its lanes).  K is the padded
+// row length (4, 8, 12 or 16); entries a >= k are identity padding, which
+// passes through every step without changing the real entries (unit pivot,
+// zero off-diagonal, zero right-hand side), so all loops run K steps.  The
+// column loops are unrolled at compile time (static_for) so that every
+// register-array index is a constant.
+
+__host__ __device__ constexpr int tri(int a, int c) { return a * (a + 1) / 2 + c; }
+
+template <int I, int N, class F>
+__device__ __forceinline__ void static_for(F&& f) {
+  if constexpr (I < N) {
+    f(std::integral_constant<int, I>{});
+    static_for<I + 1, N>(f);
+  }
+}
+
+template <int K>
+struct PointRegs {
+  float L[K * (K + 1) / 2];  // L[tri(a, c)], c <= a
+  float y[K];                // y = L^-1 K_ci, then b = L^-T y (zero for a >= k)
+  float inv[K];              // 1 / L_aa
+  float sigma;
+  bool clamped;
+};
+
+// Schur value t = K_aj - sum_{m<j} L_am L_jm with the group form's two
+// accumulators (m = 0, 2 mod 4 and m = 1, 3 mod 4 over whole blocks of four).
+template <int K, int J, int A>
+__device__ __forceinline__ float schur_value(const PointRegs<K>& p) {
+  float tv = p.L[tri(A, J)];
+  float t2 = 0.0f;
+#pragma unroll
+  for (int m = 0; m + 4 <= J; m += 4) {
+    tv = fmaf(-p.L[tri(A, m)], p.L[tri(J, m)], tv);
+    t2 = fmaf(-p.L[tri(A, m + 1)], p.L[tri(J, m + 1)], t2);
+    tv = fmaf(-p.L[tri(A, m + 2)], p.L[tri(J, m + 2)], tv);
+    t2 = fmaf(-p.L[tri(A, m + 3)], p.L[tri(J, m + 3)], t2);
+  }
+#pragma unroll
+  for (int m = (J / 4) * 4; m < J; m++) tv = fmaf(-p.L[tri(A, m)], p.L[tri(J, m)], tv);
+  return tv + t2;
+}
+
+template <int K, int KT>
+__device__ __forceinline__ void point_factor_thread(PointRegs<K>& p, int k, const KernF& kf,
+                                                    const float4 (&x)[K], float4 xq) {
+  const float k0 = kf.s2 + kf.nug;
+  static_for<0, K>([&](auto Ac) {
+    constexpr int a = decltype(Ac)::value;
+    const bool real = a < k;
+#pragma unroll
+    for (int c = 0; c < a; c++) p.L[tri(a, c)] = real ? kappa_d2<KT>(kf, sqdist(x[a], x[c])) : 0.0f;
+    p.L[tri(a, a)] = real ? k0 : 1.0f;
+    p.y[a] = real ? kappa_d2<KT>(kf, sqdist(x[a], xq)) : 0.0f;
+  });
+  DF s2{k0, 0.0f};
+  bool clamped = false;
+  const float pfloor = kPdFloor * k0;
+  static_for<0, K>([&](auto Jc) {
+    constexpr int j = decltype(Jc)::value;
+    float piv = schur_value<K, j, j>(p);
+    if (!(piv > pfloor)) {
+      piv = pfloor;
+      clamped = true;
+    }
+    const float ljj = sqrtf(piv);
+    const float inv = 1.0f / ljj;
+    static_for<j + 1, K>([&](auto Ac) {
+      constexpr int a = decltype(Ac)::value;
+      p.L[tri(a, j)] = schur_value<K, j, a>(p) * inv;
+    });
+    p.L[tri(j, j)] = ljj;
+    p.inv[j] = inv;
+    const float yj = p.y[j] * inv;
+    p.y[j] = yj;
+#pragma unroll
+    for (int a = j + 1; a < K; a++) p.y[a] = fmaf(-p.L[tri(a, j)], yj, p.y[a]);
+    s2 = df_sub_square(s2, yj);
+  });
+  float sig2 = s2.hi + s2.lo;
+  if (!(sig2 > pfloor)) {
+    sig2 = pfloor;
+    clamped = true;
+  }
+  p.clamped = clamped;
+  p.sigma = sqrtf(sig2);
+  // b = L^-T y, last entry first
+  static_for<0, K>([&](auto Jr) {
+    constexpr int j = K - 1 - decltype(Jr)::value;
+    const float bj = p.y[j] * p.inv[j];
+    p.y[j] = bj;
+#pragma unroll
+    for (int a = 0; a < j; a++) p.y[a] = fmaf(-p.L[tri(j, a)], bj, p.y[a]);
+  });
+}
+
+// Solves K_cc g = r in place with the factor of point_factor_thread (same
+// operation order as group_chol_solve); r must be zero at padding entries.
+template <int K>
+__device__ __forceinline__ void thread_chol_solve(const PointRegs<K>& p, float (&r)[K]) {
+  static_for<0, K>([&](auto Jc) {
+    constexpr int j = decltype(Jc)::value;
+    const float zj = r[j] * p.inv[j];
+    r[j] = zj;
+#pragma unroll
+    for (int a = j + 1; a < K; a++) r[a] = fmaf(-p.L[tri(a, j)], zj, r[a]);
+  });
+  static_for<0, K>([&](auto Jr) {
+    constexpr int j = K - 1 - decltype(Jr)::value;
+    const float gj = r[j] * p.inv[j];
+    r[j] = gj;
+#pragma unroll
+    for (int a = 0; a < j; a++) r[a] = fmaf(-p.L[tri(j, a)], gj, r[a]);
+  });
 }
 
 }  // namespace ggp
