@@ -208,6 +208,97 @@ __global__ void __launch_bounds__(1024) dense_chol_kernel(float* __restrict__ A,
   if (threadIdx.x == 0 && s_bad) atomicAdd(not_pd, s_bad);
 }
 
+// Dense block with the lower triangle held in shared memory (n0 <= 320): one
+// block of 1024 threads, four threads per row for every dot product.
+//   Cholesky, left-looking by columns: t_r = A_rj - sum_{m<j} L_rm L_jm for
+//   r >= j, pivot t_j (floored at 1e-7 K_00 and counted), L_rj = t_r / L_jj.
+//   Inverse in place, last column first: with the trailing block already
+//   inverted (W2), column j of W = L^-1 is W_jj = 1 / L_jj and
+//   W_rj = -W_jj sum_{j<m<=r} W2_rm L_mj for r > j.
+// Outputs as dense_chol_kernel: L0 and L0^-1 row-major with zero upper part,
+// sigma_i = L0_ii, logdet += sum log L0_ii^2 (FP64), not-PD count.
+constexpr int kDenseSmemMax = 320;
+__device__ __forceinline__ int tri_ix(int r, int c) { return r * (r + 1) / 2 + c; }
+
+__global__ void __launch_bounds__(1024) dense_chol_smem_kernel(float* __restrict__ A,
+                                                               float* __restrict__ W, int n0,
+                                                               float* __restrict__ sigma,
+                                                               double* __restrict__ logdet,
+                                                               unsigned long long* __restrict__ not_pd) {
+  extern __shared__ float S[];         // [tri(n0)] packed lower triangle
+  float* tr = S + n0 * (n0 + 1) / 2;   // [n0] column values of one step
+  __shared__ unsigned long long s_bad;
+  const int w = threadIdx.x >> 2, part = threadIdx.x & 3;
+  if (threadIdx.x == 0) s_bad = 0;
+  for (int e = threadIdx.x; e < n0 * n0; e += blockDim.x) {
+    const int r = e / n0, c = e - r * n0;
+    if (c <= r) S[tri_ix(r, c)] = A[e];
+  }
+  __syncthreads();
+  const float fl = kPdFloor * S[0];
+  for (int j = 0; j < n0; j++) {
+    const float* Lj = S + tri_ix(j, 0);
+    for (int r0 = 0; r0 < n0; r0 += 256) {
+      const int r = r0 + w;
+      float acc = 0.0f;
+      if (r >= j && r < n0) {
+        const float* Lr = S + tri_ix(r, 0);
+        for (int m = part; m < j; m += 4) acc = fmaf(Lr[m], Lj[m], acc);
+      }
+      acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+      acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+      if (part == 0 && r >= j && r < n0) tr[r] = S[tri_ix(r, j)] - acc;
+    }
+    __syncthreads();
+    float piv = tr[j];
+    const bool bad = !(piv > fl);
+    if (bad) piv = fl;
+    const float ljj = sqrtf(piv);
+    const float inv = 1.0f / ljj;
+    for (int r = j + 1 + threadIdx.x; r < n0; r += blockDim.x) S[tri_ix(r, j)] = tr[r] * inv;
+    if (threadIdx.x == 0) {
+      S[tri_ix(j, j)] = ljj;
+      if (bad) s_bad++;
+    }
+    __syncthreads();
+  }
+  double lsum = 0.0;
+  for (int e = threadIdx.x; e < n0 * n0; e += blockDim.x) {
+    const int r = e / n0, c = e - r * n0;
+    A[e] = c <= r ? S[tri_ix(r, c)] : 0.0f;
+  }
+  for (int i = threadIdx.x; i < n0; i += blockDim.x) {
+    const float l = S[tri_ix(i, i)];
+    sigma[i] = l;
+    lsum += log((double)l * (double)l);
+  }
+  __syncthreads();
+  for (int j = n0 - 1; j >= 0; j--) {
+    const float d = 1.0f / S[tri_ix(j, j)];
+    for (int r0 = 0; r0 < n0; r0 += 256) {
+      const int r = r0 + w;
+      float acc = 0.0f;
+      if (r > j && r < n0) {
+        const float* Wr = S + tri_ix(r, 0);
+        for (int m = j + 1 + part; m <= r; m += 4) acc = fmaf(Wr[m], S[tri_ix(m, j)], acc);
+      }
+      acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+      acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+      if (part == 0 && r > j && r < n0) tr[r] = -d * acc;
+    }
+    __syncthreads();
+    for (int r = j + 1 + threadIdx.x; r < n0; r += blockDim.x) S[tri_ix(r, j)] = tr[r];
+    if (threadIdx.x == 0) S[tri_ix(j, j)] = d;
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < n0 * n0; e += blockDim.x) {
+    const int r = e / n0, c = e - r * n0;
+    W[e] = c <= r ? S[tri_ix(r, c)] : 0.0f;
+  }
+  block_add_double(lsum, logdet);
+  if (threadIdx.x == 0 && s_bad) atomicAdd(not_pd, s_bad);
+}
+
 template <int G>
 int launch_point(int type, graphgp_graph_t g, graphgp_factor_t f, const KernF& kf,
                  cudaStream_t s) {
@@ -273,8 +364,16 @@ int dense_factor(graphgp_graph_t g, graphgp_factor_t f, const KernF& kf, int typ
     default: dense_fill_kernel<GRAPHGP_SQEXP><<<grid, 256, 0, s>>>(g->xs, n0, kf, f->L0); break;
   }
   GGP_CUDA(cudaGetLastError());
-  dense_chol_kernel<<<1, 1024, n0 * sizeof(float), s>>>(f->L0, f->L0inv, n0, f->sigma, f->logdet,
-                                                        f->not_pd);
+  if (n0 <= kDenseSmemMax) {
+    const size_t smem = ((size_t)n0 * (n0 + 1) / 2 + n0) * sizeof(float);
+    GGP_CUDA(cudaFuncSetAttribute(dense_chol_smem_kernel,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    dense_chol_smem_kernel<<<1, 1024, smem, s>>>(f->L0, f->L0inv, n0, f->sigma, f->logdet,
+                                                 f->not_pd);
+  } else {
+    dense_chol_kernel<<<1, 1024, n0 * sizeof(float), s>>>(f->L0, f->L0inv, n0, f->sigma,
+                                                          f->logdet, f->not_pd);
+  }
   GGP_CUDA(cudaGetLastError());
   return GRAPHGP_OK;
 }

@@ -188,9 +188,10 @@ template <int K>
 struct PointRegs {
   float L[K * (K + 1) / 2];  // L[tri(a, c)], c <= a
   float y[K];                // y = L^-1 K_ci, then b = L^-T y (zero for a >= k)
-  float inv[K];              // 1 / L_aa
   float sigma;
   bool clamped;
+  // 1 / L_jj, recomputed where needed (the same correctly rounded quotient)
+  __device__ __forceinline__ float inv(int j) const { return 1.0f / L[tri(j, j)]; }
 };
 
 // Schur value t = K_aj - sum_{m<j} L_am L_jm with the group form's two
@@ -215,8 +216,9 @@ template <int K, int KT>
 __device__ __forceinline__ void point_factor_thread(PointRegs<K>& p, int k, const KernF& kf,
                                                     const float4 (&x)[K], float4 xq) {
   const float k0 = kf.s2 + kf.nug;
-  static_for<0, K>([&](auto Ac) {
-    constexpr int a = decltype(Ac)::value;
+  // last row first: coordinates x_a die as soon as row a is filled
+  static_for<0, K>([&](auto Ar) {
+    constexpr int a = K - 1 - decltype(Ar)::value;
     const bool real = a < k;
 #pragma unroll
     for (int c = 0; c < a; c++) p.L[tri(a, c)] = real ? kappa_d2<KT>(kf, sqdist(x[a], x[c])) : 0.0f;
@@ -240,7 +242,6 @@ __device__ __forceinline__ void point_factor_thread(PointRegs<K>& p, int k, cons
       p.L[tri(a, j)] = schur_value<K, j, a>(p) * inv;
     });
     p.L[tri(j, j)] = ljj;
-    p.inv[j] = inv;
     const float yj = p.y[j] * inv;
     p.y[j] = yj;
 #pragma unroll
@@ -257,7 +258,7 @@ __device__ __forceinline__ void point_factor_thread(PointRegs<K>& p, int k, cons
   // b = L^-T y, last entry first
   static_for<0, K>([&](auto Jr) {
     constexpr int j = K - 1 - decltype(Jr)::value;
-    const float bj = p.y[j] * p.inv[j];
+    const float bj = p.y[j] * p.inv(j);
     p.y[j] = bj;
 #pragma unroll
     for (int a = 0; a < j; a++) p.y[a] = fmaf(-p.L[tri(j, a)], bj, p.y[a]);
@@ -270,14 +271,14 @@ template <int K>
 __device__ __forceinline__ void thread_chol_solve(const PointRegs<K>& p, float (&r)[K]) {
   static_for<0, K>([&](auto Jc) {
     constexpr int j = decltype(Jc)::value;
-    const float zj = r[j] * p.inv[j];
+    const float zj = r[j] * p.inv(j);
     r[j] = zj;
 #pragma unroll
     for (int a = j + 1; a < K; a++) r[a] = fmaf(-p.L[tri(a, j)], zj, r[a]);
   });
   static_for<0, K>([&](auto Jr) {
     constexpr int j = K - 1 - decltype(Jr)::value;
-    const float gj = r[j] * p.inv[j];
+    const float gj = r[j] * p.inv(j);
     r[j] = gj;
 #pragma unroll
     for (int a = 0; a < j; a++) r[a] = fmaf(-p.L[tri(j, a)], gj, r[a]);

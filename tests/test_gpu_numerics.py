@@ -108,6 +108,22 @@ def test_all_dense(gpu_lib):
     assert rel_norm(v, oracle.generate(fo, want["nbr_pos"], 8, 300, xi.astype(np.float64))) < 1e-4
 
 
+@pytest.mark.parametrize("n0", [17, 320, 321, 700])
+def test_dense_block_sizes(gpu_lib, n0):
+    """Dense blocks held in shared memory (n0 <= 320) and in global memory
+    (n0 > 320): L0, L0^-1 (through whiten) and the sweeps against the oracle."""
+    N, k = 3000, 8
+    pts = workloads.uniform_cube(N, 50 + n0)
+    g, f, want, fo = _setup(gpu_lib, pts, k, KERNELS["m32"], n0=n0)
+    _check_factor(gpu_lib, g, f, want, fo)
+    xi = workloads.white_noise(N, 7)
+    v = np_(gpu_lib.generate(g, f, to_gpu(xi)))
+    assert rel_norm(v, oracle.generate(fo, want["nbr_pos"], k, n0, xi.astype(np.float64))) < 1e-4
+    v_in = v.astype(np.float32)
+    xi_or = oracle.whiten(fo, want["nbr_pos"], k, n0, v_in.astype(np.float64))
+    assert rel_norm(np_(gpu_lib.whiten(g, f, to_gpu(v_in))), xi_or) < 1e-4
+
+
 def test_duplicate_points_without_nugget_flag_not_pd(gpu_lib):
     base = workloads.uniform_cube(1000, 9)
     pts = np.concatenate([base, base])
