@@ -305,6 +305,90 @@ __global__ void __launch_bounds__(128) factor_backward_kernel(
   block_add3(tl, ts, tn, thetabar);
 }
 
+// The same per-row backward with one thread per point and the factor in
+// registers (k <= 16, K = padded row length), recomputed by
+// point_factor_thread: bit-identical b and sigma to the forward kernel.  Once
+// g = K_cc^-1 bbar is solved, L is dead and the coordinates are reloaded for
+// the kernel derivatives; the pair (a, c), c < a, takes Kbar_ac + Kbar_ca
+// against the symmetric dkappa_ac.  Each row's sum (FP32, at most k + 1
+// terms) goes straight into the thread's FP64 totals.
+template <int K, int KT>
+__global__ void __launch_bounds__(128) factor_backward_thread_kernel(
+    const float4* __restrict__ xs, const int32_t* __restrict__ nbr, int64_t N, int k, int64_t n0,
+    KernF kf, int mode, const float* __restrict__ coef, float beta, const float* __restrict__ v,
+    const float* __restrict__ xi, float* __restrict__ xibar_out, double* __restrict__ thetabar) {
+  double tl = 0.0, ts = 0.0, tn = 0.0;
+  const int64_t npts = N - n0;
+  const float inv_s2 = 1.0f / kf.s2;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < npts;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = n0 + t;
+    const int4* row = reinterpret_cast<const int4*>(nbr + t * K);
+    const float4 xq = __ldg(xs + i);
+    PointRegs<K> p;
+    {
+      float4 x[K];
+#pragma unroll
+      for (int q = 0; q < K / 4; q++) {
+        const int4 c = __ldg(row + q);
+        x[4 * q] = __ldg(xs + c.x);
+        x[4 * q + 1] = __ldg(xs + c.y);
+        x[4 * q + 2] = __ldg(xs + c.z);
+        x[4 * q + 3] = __ldg(xs + c.w);
+      }
+      point_factor_thread<K, KT>(p, k, kf, x, xq);
+    }
+    const float sigma = p.sigma;
+    const float ci = coef[i];
+    const float alpha = mode == 0 ? -ci / sigma : ci;
+    const float sigbar = alpha * xi[i] + beta / sigma;
+    const float sbar = sigbar / (2.0f * sigma);
+    float g[K];
+    int32_t ca[K];
+#pragma unroll
+    for (int q = 0; q < K / 4; q++) {
+      const int4 c = __ldg(row + q);
+      ca[4 * q] = c.x;
+      ca[4 * q + 1] = c.y;
+      ca[4 * q + 2] = c.z;
+      ca[4 * q + 3] = c.w;
+    }
+#pragma unroll
+    for (int a = 0; a < K; a++) g[a] = a < k ? alpha * v[ca[a]] : 0.0f;
+    thread_chol_solve<K>(p, g);
+    const float* bb = p.y;
+    // row sums in FP32 (at most k + 1 terms), added to the FP64 totals
+    ts += sbar;  // Kbar_ii = sbar
+    tn += sbar;
+    float4 x[K];
+#pragma unroll
+    for (int a = 0; a < K; a++) x[a] = a < k ? __ldg(xs + ca[a]) : xq;
+#pragma unroll
+    for (int a = 0; a < K; a++) {
+      if (a < k) {
+        const float kaa = -g[a] * bb[a] + sbar * bb[a] * bb[a];
+        float pl = 0.0f, ps = kaa;
+#pragma unroll
+        for (int c = 0; c < a; c++) {
+          const float kb = (-g[a] * bb[c] + sbar * bb[a] * bb[c]) + (-g[c] * bb[a] + sbar * bb[c] * bb[a]);
+          const float d2 = sqdist(x[a], x[c]);
+          ps += kb * kappa_d2<KT>(kf, d2) * inv_s2;
+          pl += kb * dkappa_dell_d2<KT>(kf, d2);
+        }
+        const float kci = g[a] - 2.0f * sbar * bb[a];
+        const float d2q = sqdist(x[a], xq);
+        ps += kci * kappa_d2<KT>(kf, d2q) * inv_s2;
+        pl += kci * dkappa_dell_d2<KT>(kf, d2q);
+        tl += pl;
+        ts += ps;
+        tn += kaa;
+      }
+    }
+    if (mode == 1) xibar_out[i] = sigma * ci;
+  }
+  block_add3(tl, ts, tn, thetabar);
+}
+
 __global__ void scale_kernel(const float* __restrict__ x, float s, float* __restrict__ y,
                              int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -336,12 +420,39 @@ int launch_factor_backward(graphgp_graph_t g, graphgp_factor_t f, int mode, cons
   return GRAPHGP_OK;
 }
 
+template <int K>
+int launch_factor_backward_thread(graphgp_graph_t g, graphgp_factor_t f, int mode,
+                                  const float* coef, float beta, const float* v, const float* xi,
+                                  float* xibar, double* thetabar, cudaStream_t s) {
+  const int64_t npts = g->N - g->n0;
+  if (npts <= 0) return GRAPHGP_OK;
+  const unsigned grid = grid_for(npts, 128, 8);
+  KernF kf = make_kernf(f->kern);
+#define GGP_FBT(KT)                                                                             \
+  factor_backward_thread_kernel<K, KT><<<grid, 128, 0, s>>>(g->xs, g->nbr, g->N, g->k, g->n0, kf, \
+                                                            mode, coef, beta, v, xi, xibar,      \
+                                                            thetabar)
+  switch (f->kern.type) {
+    case GRAPHGP_MATERN12: GGP_FBT(GRAPHGP_MATERN12); break;
+    case GRAPHGP_MATERN32: GGP_FBT(GRAPHGP_MATERN32); break;
+    case GRAPHGP_MATERN52: GGP_FBT(GRAPHGP_MATERN52); break;
+    default: GGP_FBT(GRAPHGP_SQEXP); break;
+  }
+#undef GGP_FBT
+  GGP_CUDA(cudaGetLastError());
+  return GRAPHGP_OK;
+}
+
 int factor_backward(graphgp_graph_t g, graphgp_factor_t f, int mode, const float* coef,
                     float beta, const float* v, const float* xi, float* xibar, double* thetabar,
                     cudaStream_t s) {
-  if (g->k <= 8) return launch_factor_backward<8>(g, f, mode, coef, beta, v, xi, xibar, thetabar, s);
-  if (g->k <= 16) return launch_factor_backward<16>(g, f, mode, coef, beta, v, xi, xibar, thetabar, s);
-  return launch_factor_backward<32>(g, f, mode, coef, beta, v, xi, xibar, thetabar, s);
+  switch (g->kp) {
+    case 4: return launch_factor_backward_thread<4>(g, f, mode, coef, beta, v, xi, xibar, thetabar, s);
+    case 8: return launch_factor_backward_thread<8>(g, f, mode, coef, beta, v, xi, xibar, thetabar, s);
+    case 12: return launch_factor_backward_thread<12>(g, f, mode, coef, beta, v, xi, xibar, thetabar, s);
+    case 16: return launch_factor_backward_thread<16>(g, f, mode, coef, beta, v, xi, xibar, thetabar, s);
+    default: return launch_factor_backward<32>(g, f, mode, coef, beta, v, xi, xibar, thetabar, s);
+  }
 }
 
 // Dense block backward from Lbar0 (built from u, xi_0 by dense_lbar_kernel).

@@ -16,6 +16,8 @@ CASES = [
     ("uniform", 3000, 8, (1, 1.0, 0.1, 1e-4)),
     # the differentiation workload's kernel at N = 2^12: SE, l = 0.03, nugget 1e-4, k = 32
     ("uniform", 4096, 32, (3, 1.0, 0.03, 1e-4)),
+    # the same kernel at k = 16 (one thread per point in the recompute)
+    ("uniform", 4096, 16, (3, 1.0, 0.03, 1e-4)),
     ("gaussian", 3000, 16, (1, 1.0, 0.1, 1e-6)),
     ("ldr", 3000, 5, (2, 1.2, 0.1, 1e-3)),
 ]
