@@ -76,13 +76,16 @@ typedef struct {
                          line "dense initial batch"); 0 = default
                          min(N, max(k, 256)) */
   int32_t split_rule; /* k-d split dimension: 0 = widest bounding-box extent
-                         (ties to the lowest dimension), 1 = level mod 3 */
+                         (ties to the lowest dimension), 1 = level mod 3
+                         (d = 3 only) */
   int64_t max_spin;   /* bound on device spin iterations; 0 = default */
 } graphgp_build_opts;
 
 /* ---- graph construction (Sec. 2.2, Sec. 2.3 last paragraph) ------------
- * Builds the bit-reversed left-balanced k-d tree over points_d (float[N][3],
- * input order), the k nearest PRECEDING neighbours of every point with tree
+ * Builds the bit-reversed left-balanced k-d tree over points_d (float[N][d],
+ * d = 1, 2 or 3, row-major, input order; points of d < 3 are held as 3-D
+ * points with zero in the missing coordinates, which changes no distance and
+ * no split), the k nearest PRECEDING neighbours of every point with tree
  * index >= n0 (key: FP32 squared distance, ties to the lower tree index),
  * the depth of every point (d_i = 1 + max over c(i), dense block = 0), and
  * the depth-sorted graph order (ties by k-d tree in-order rank).

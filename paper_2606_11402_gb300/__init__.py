@@ -219,12 +219,14 @@ class Factor:
 # --- entry points ------------------------------------------------------------
 def build_graph(points: torch.Tensor, k: int, n0: int = 0, split_rule: int = 0,
                 max_spin: int = 0, stream=None) -> Graph:
-    """graphgp_build_graph: points float32[N, 3] on the GPU (input order)."""
-    if points.dim() != 2 or points.shape[1] != 3:
-        raise ValueError("points must be [N, 3]")
+    """graphgp_build_graph: points float32[N, d], d in {1, 2, 3}, on the GPU
+    (input order)."""
+    if points.dim() != 2 or points.shape[1] not in (1, 2, 3):
+        raise ValueError("points must be [N, d] with d in {1, 2, 3}")
     h = ctypes.c_void_p()
     opts = _BuildOpts(int(n0), int(split_rule), int(max_spin))
-    _check(load().graphgp_build_graph(_dev(points, torch.float32), points.shape[0], 3, int(k),
+    _check(load().graphgp_build_graph(_dev(points, torch.float32), points.shape[0],
+                                      points.shape[1], int(k),
                                       ctypes.byref(opts), _stream(stream), ctypes.byref(h)),
            "build_graph")
     return Graph(h)

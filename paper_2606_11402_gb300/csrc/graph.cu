@@ -13,14 +13,20 @@
 namespace ggp {
 namespace {
 
-__global__ void canonicalise_kernel(const float* __restrict__ in, float* __restrict__ out,
+// Points of dimension d <= 3 become 3-D points with zero in the missing
+// coordinates: distances are unchanged (exact zero terms), and the widest-
+// extent split never picks a zero-extent dimension while a real one has a
+// positive extent (all extents zero: lowest dimension, as in d dimensions).
+__global__ void canonicalise_kernel(const float* __restrict__ in, int d, float* __restrict__ out,
                                     int64_t n, unsigned long long* __restrict__ bad) {
   unsigned long long local = 0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    float x = in[i];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * 3;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / 3;
+    const int c = (int)(e - i * 3);
+    float x = c < d ? in[i * d + c] : 0.0f;
     if (!isfinite(x)) local++;
-    out[i] = (x == 0.0f) ? 0.0f : x;  // -0.0 becomes +0.0
+    out[e] = (x == 0.0f) ? 0.0f : x;  // -0.0 becomes +0.0
   }
   if (local) atomicAdd(bad, local);
 }
@@ -242,11 +248,12 @@ extern "C" int graphgp_build_graph(const float* points_d, int64_t N, int d, int 
                                    graphgp_graph_t* out) {
   if (!out) return GRAPHGP_ERR_INVALID;
   *out = nullptr;
-  if (!points_d || N < 1 || N >= ((int64_t)1 << 31) || d != 3 || k < 1 || k > 32)
+  if (!points_d || N < 1 || N >= ((int64_t)1 << 31) || d < 1 || d > 3 || k < 1 || k > 32)
     return GRAPHGP_ERR_INVALID;
   int n0 = opts && opts->n0 > 0 ? opts->n0 : (int)std::min<int64_t>(N, std::max(k, 256));
   int rule = opts ? opts->split_rule : 0;
-  if (n0 < k || n0 > N || n0 > 2048 || (rule != 0 && rule != 1)) return GRAPHGP_ERR_INVALID;
+  if (n0 < k || n0 > N || n0 > 2048 || (rule != 0 && rule != 1) || (rule == 1 && d != 3))
+    return GRAPHGP_ERR_INVALID;
   cudaStream_t s = (cudaStream_t)stream;
   graphgp_graph_t g = new (std::nothrow) graphgp_graph_s();
   if (!g) return GRAPHGP_ERR_OOM;
@@ -268,7 +275,7 @@ extern "C" int graphgp_build_graph(const float* points_d, int64_t N, int d, int 
     GGP_TRY(sc.alloc(&bad, 1));
     GGP_CUDA(cudaMemsetAsync(bad, 0, 8, s));
     GGP_CUDA(cudaMemsetAsync(g->err, 0, 4, s));
-    canonicalise_kernel<<<grid_for(N * 3, 256), 256, 0, s>>>(points_d, g->pts_in, N * 3, bad);
+    canonicalise_kernel<<<grid_for(N * 3, 256), 256, 0, s>>>(points_d, d, g->pts_in, N, bad);
     GGP_CUDA(cudaGetLastError());
     unsigned long long nbad = 0;
     GGP_CUDA(cudaMemcpyAsync(&nbad, bad, 8, cudaMemcpyDeviceToHost, s));

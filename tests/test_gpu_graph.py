@@ -83,6 +83,25 @@ def test_graph_larger_bit_exact(gpu_lib):
     _compare(gpu_lib, pts, 16, knn="tree")
 
 
+@pytest.mark.parametrize("d", [1, 2])
+@pytest.mark.parametrize("kind", ["gaussian", "grid"])
+def test_graph_lower_dimensions(gpu_lib, d, kind):
+    """float[N][d] input, d < 3: the same graph as the oracle's on the points
+    padded with zero coordinates (the d-dimensional definition)."""
+    N, k = 5003, 8
+    pts3 = _cloud(kind, N, 70 + d)
+    pts_d = np.ascontiguousarray(pts3[:, :d])
+    padded = np.zeros((N, 3), np.float32)
+    padded[:, :d] = pts_d
+    want = oracle.build_graph(padded, k, 64)
+    g = gpu_lib.build_graph(to_gpu(pts_d), k, n0=64)
+    got = gpu_graph_arrays(g)
+    for key in ("tree_point", "split_dim", "nbr_tree", "depth", "order", "level_offsets", "nbr_pos"):
+        assert np.array_equal(got[key], want[key]), key
+    with pytest.raises(gpu_lib.GraphGPError):  # round-robin splits need d = 3
+        gpu_lib.build_graph(to_gpu(pts_d), k, n0=64, split_rule=1)
+
+
 def test_graph_rejects_bad_input(gpu_lib):
     pts = workloads.uniform_cube(100, 1)
     pts[5, 1] = np.nan

@@ -108,6 +108,25 @@ def test_all_dense(gpu_lib):
     assert rel_norm(v, oracle.generate(fo, want["nbr_pos"], 8, 300, xi.astype(np.float64))) < 1e-4
 
 
+@pytest.mark.parametrize("d", [1, 2])
+def test_factor_and_sweeps_lower_dimensions(gpu_lib, d):
+    """A 2-D (1-D) cloud: factor, generate and whiten against the oracle on the
+    zero-padded points."""
+    N, k = 6000, 8
+    pts = workloads.uniform_cube(N, 80 + d)
+    pts[:, d:] = 0.0
+    want = oracle.build_graph(pts, k, 64)
+    g = gpu_lib.build_graph(to_gpu(np.ascontiguousarray(pts[:, :d])), k, n0=64)
+    kern = (1, 1.0, 0.05, 1e-5)
+    fo = oracle.factor(want["pts_pos"], want["nbr_pos"], k, 64, oracle.Kernel(*kern))
+    f = gpu_lib.factor(g, gpu_lib.Kernel(*kern))
+    tol = fp32_tolerance(want, kern)
+    _check_factor(gpu_lib, g, f, want, fo, tol)
+    xi = workloads.white_noise(N, 9)
+    v = np_(gpu_lib.generate(g, f, to_gpu(xi)))
+    assert rel_norm(v, oracle.generate(fo, want["nbr_pos"], k, 64, xi.astype(np.float64))) < tol[0]
+
+
 @pytest.mark.parametrize("n0", [17, 320, 321, 700])
 def test_dense_block_sizes(gpu_lib, n0):
     """Dense blocks held in shared memory (n0 <= 320) and in global memory

@@ -161,3 +161,68 @@ def test_bitreversed_order_gives_fewer_batches():
     assert _levels_for_order(pts, g["tree_point"], k, n0) == ours
     assert ours < min(std, rnd, xs)
     assert 1.5 * ours < std and 1.5 * ours < xs
+
+
+def _tree_d(pts, d):
+    """The tree fill of Sec. 2.2 written directly in d dimensions: widest FP32
+    extent among the d coordinates (ties to the lowest), median by
+    (coordinate, input index), node j takes the entry after its left subtree."""
+    N = pts.shape[0]
+    level = lambda j: (j + 1).bit_length() - 1
+    left = lambda j: j + 2 ** level(j)
+    right = lambda j: j + 2 ** (level(j) + 1)
+    size = {}
+
+    def sz(j):
+        if j >= N:
+            return 0
+        if j not in size:
+            size[j] = 1 + sz(left(j)) + sz(right(j))
+        return size[j]
+
+    tp = np.full(N, -1, np.int64)
+
+    def fill(j, S):
+        if j >= N:
+            assert not S
+            return
+        ext = [np.float32(max(pts[i, c] for i in S)) - np.float32(min(pts[i, c] for i in S))
+               for c in range(d)]
+        dim = int(np.argmax(ext))  # first maximum: lowest dimension on ties
+        S = sorted(S, key=lambda i: (pts[i, dim], i))
+        m = sz(left(j))
+        tp[j] = S[m]
+        fill(left(j), S[:m])
+        fill(right(j), S[m + 1:])
+
+    fill(0, list(range(N)))
+    return tp
+
+
+def _exact_key_d(a, b, d):
+    """FP32 key in d dimensions: dx = fl(a - b), t = fl(dx^2), then
+    t = fl(dy^2 + t) for the second coordinate."""
+    F = lambda x: Fraction(float(x))
+    t = None
+    for c in range(d):
+        dc = _round_f32(F(a[c]) - F(b[c]))
+        t = _round_f32(F(dc) * F(dc) + (F(t) if t is not None else 0))
+    return t
+
+
+@pytest.mark.parametrize("d", [1, 2])
+def test_lower_dimensions_equal_zero_padded_points(d):
+    """Points of dimension d < 3 are handled as 3-D points with zero extra
+    coordinates: the padded tree and neighbour lists equal the d-dimensional
+    definitions (with ties: coordinates on a coarse grid)."""
+    N, k, n0 = 120, 4, 5
+    rng = np.random.default_rng(30 + d)
+    pts_d = (rng.integers(0, 40, size=(N, d)) * 0.05).astype(np.float32)
+    padded = np.zeros((N, 3), np.float32)
+    padded[:, :d] = pts_d
+    g = oracle.build_graph(padded, k, n0)
+    tp = _tree_d(pts_d, d)
+    assert np.array_equal(g["tree_point"], tp)
+    for j in range(n0, N):
+        keys = sorted((_exact_key_d(pts_d[tp[i]], pts_d[tp[j]], d), i) for i in range(j))
+        assert g["nbr_tree"][j - n0].tolist() == [i for _, i in keys[:k]]
