@@ -192,6 +192,32 @@ int graphgp_nll(graphgp_graph_t g, graphgp_factor_t f, const float* v_d,
 int graphgp_nll_noalloc(graphgp_graph_t g, graphgp_factor_t f, const float* v_d,
                         double* out_d, void* stream);
 
+/* ---- on-the-fly sweeps (Alg. 1 as printed: factors never stored) --------
+ * The same operators as graphgp_generate / graphgp_whiten / graphgp_nll with
+ * the conditioning factor of every point (Sec. 2.1 Eq. 2) recomputed inside
+ * the pass from the coordinates and `kern` (same validity rules as
+ * graphgp_factor), so no graphgp_factor_t is needed and the device holds the
+ * graph alone (about k + 4 words per point instead of 2k + 5).  For kernel
+ * parameters that change at every step.  Requires k <= 16, else
+ * GRAPHGP_ERR_INVALID.  Results are bit-identical to graphgp_factor followed
+ * by the stored-factor sweep (the factor and the dot products run in the same
+ * order); the log-determinant equals graphgp_logdet up to the order of its
+ * FP64 partial sums.
+ *   generate_fused: v_d = L xi_d.
+ *   whiten_fused:   xi_d = L^-1 v_d; logdet_d (nullable, double, device) is
+ *                   overwritten with log det(L L^T).
+ *   nll_fused:      nll_d[0] = 0.5 xi.xi + 0.5 logdet (uses the graph's work
+ *                   vector; do not overlap with other calls on the graph).
+ * not_pd_d (nullable, uint64 on the device) has the number of floored pivots
+ * ADDED to it.  Each call allocates stream-ordered scratch for the dense
+ * block (2 n0^2 floats). */
+int graphgp_generate_fused(graphgp_graph_t g, const graphgp_kernel* kern, const float* xi_d,
+                           float* v_d, uint64_t* not_pd_d, void* stream);
+int graphgp_whiten_fused(graphgp_graph_t g, const graphgp_kernel* kern, const float* v_d,
+                         float* xi_d, double* logdet_d, uint64_t* not_pd_d, void* stream);
+int graphgp_nll_fused(graphgp_graph_t g, const graphgp_kernel* kern, const float* v_d,
+                      double* nll_d, uint64_t* not_pd_d, void* stream);
+
 /* ---- adjoints (Sec. 2.3 "forward and backward derivatives") -------------
  * Vector-Jacobian products.  thetabar_d is double[3] =
  * [d/d lengthscale, d/d sigma2, d/d nugget] and is ACCUMULATED (+=).  The

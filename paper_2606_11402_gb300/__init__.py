@@ -93,6 +93,9 @@ def load() -> ctypes.CDLL:
             "graphgp_whiten_backward": [_P, _P, _P, _P, _P, ctypes.c_double, _P, _P, _P],
             "graphgp_nll_backward": [_P, _P, _P, ctypes.c_double, _P, _P, _P],
             "graphgp_selftest_wait_timeout": [_I64, _P],
+            "graphgp_generate_fused": [_P, _P, _P, _P, _P, _P],
+            "graphgp_whiten_fused": [_P, _P, _P, _P, _P, _P, _P],
+            "graphgp_nll_fused": [_P, _P, _P, _P, _P, _P],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -297,6 +300,53 @@ def nll(graph: Graph, fac: Factor, v: torch.Tensor, out: torch.Tensor | None = N
     o = torch.empty(1, dtype=torch.float64, device="cuda") if out is None else out
     _check(load().graphgp_nll(graph.handle, fac.handle, _dev(v, torch.float32, graph.N, "v"),
                               _dev(o, torch.float64, 1), _stream(stream)), "nll")
+    return o
+
+
+def _opt(t, dtype, n, what):
+    return None if t is None else _dev(t, dtype, n, what)
+
+
+def generate_fused(graph: Graph, kernel: Kernel, xi: torch.Tensor, out: torch.Tensor | None = None,
+                   not_pd: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """graphgp_generate_fused: v = L xi with the factors recomputed in the pass
+    (k <= 16); not_pd (int64[1], optional) has the floored pivots added."""
+    v = torch.empty_like(xi) if out is None else out
+    kc = kernel._c()
+    _check(load().graphgp_generate_fused(graph.handle, ctypes.byref(kc),
+                                         _dev(xi, torch.float32, graph.N, "xi"),
+                                         _dev(v, torch.float32, graph.N, "v"),
+                                         _opt(not_pd, torch.int64, 1, "not_pd"), _stream(stream)),
+           "generate_fused")
+    return v
+
+
+def whiten_fused(graph: Graph, kernel: Kernel, v: torch.Tensor, out: torch.Tensor | None = None,
+                 logdet: torch.Tensor | None = None, not_pd: torch.Tensor | None = None,
+                 stream=None) -> torch.Tensor:
+    """graphgp_whiten_fused: xi = L^-1 v with the factors recomputed in the
+    pass; logdet (float64[1], optional) receives log det(L L^T)."""
+    xi = torch.empty_like(v) if out is None else out
+    kc = kernel._c()
+    _check(load().graphgp_whiten_fused(graph.handle, ctypes.byref(kc),
+                                       _dev(v, torch.float32, graph.N, "v"),
+                                       _dev(xi, torch.float32, graph.N, "xi"),
+                                       _opt(logdet, torch.float64, 1, "logdet"),
+                                       _opt(not_pd, torch.int64, 1, "not_pd"), _stream(stream)),
+           "whiten_fused")
+    return xi
+
+
+def nll_fused(graph: Graph, kernel: Kernel, v: torch.Tensor, out: torch.Tensor | None = None,
+              not_pd: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """graphgp_nll_fused: 0.5 xi.xi + 0.5 logdet without a stored factor."""
+    o = torch.empty(1, dtype=torch.float64, device="cuda") if out is None else out
+    kc = kernel._c()
+    _check(load().graphgp_nll_fused(graph.handle, ctypes.byref(kc),
+                                    _dev(v, torch.float32, graph.N, "v"),
+                                    _dev(o, torch.float64, 1, "nll"),
+                                    _opt(not_pd, torch.int64, 1, "not_pd"), _stream(stream)),
+           "nll_fused")
     return o
 
 

@@ -268,4 +268,8 @@ int point_factor(graphgp_graph_t g, graphgp_factor_t f, const KernF& kp,
 
 int build_child_csr(graphgp_graph_t g, cudaStream_t s);
 
+// y = M x for the n0 x n0 row-major lower-triangular M (the dense block's
+// L0 or L0^-1); adds sum y_i^2 to *sq when sq is given.
+int dense_matvec(const float* M, const float* x, float* y, int n0, double* sq, cudaStream_t s);
+
 }  // namespace ggp

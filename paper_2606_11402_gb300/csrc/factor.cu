@@ -19,32 +19,6 @@
 namespace ggp {
 namespace {
 
-// Running product of sigma^2 values in FP64 with a separate binary exponent.
-struct LogAcc {
-  double m = 1.0;
-  int e = 0;
-  __device__ void mul(float sigma) {
-    m *= (double)sigma * (double)sigma;
-    int ex;
-    m = frexp(m, &ex);
-    e += ex;
-  }
-  __device__ double log_value() const { return log(m) + (double)e * 0.69314718055994530942; }
-};
-
-__device__ void block_add_double(double v, double* out) {
-  __shared__ double red[32];
-  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  int w = threadIdx.x >> 5;
-  if ((threadIdx.x & 31) == 0) red[w] = v;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int i = 0; i < (int)(blockDim.x >> 5); i++) s += red[i];
-    atomicAdd(out, s);
-  }
-}
-
 template <int G, int KT>
 __global__ void __launch_bounds__(128) point_factor_kernel(
     const float4* __restrict__ xs, const int32_t* __restrict__ nbr, int64_t N, int k, int kp,

@@ -21,6 +21,34 @@ namespace ggp {
 
 constexpr float kPdFloor = 1e-7f;
 
+// Running product of sigma^2 values in FP64 with a separate binary exponent
+// (one log per thread at the end).
+struct LogAcc {
+  double m = 1.0;
+  int e = 0;
+  __device__ void mul(float sigma) {
+    m *= (double)sigma * (double)sigma;
+    int ex;
+    m = frexp(m, &ex);
+    e += ex;
+  }
+  __device__ double log_value() const { return log(m) + (double)e * 0.69314718055994530942; }
+};
+
+// Block-wide FP64 sum (blockDim.x a multiple of 32, at most 1024), added to *out.
+__device__ inline void block_add_double(double v, double* out) {
+  __shared__ double red[32];
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) red[w] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); i++) s += red[i];
+    atomicAdd(out, s);
+  }
+}
+
 struct DF {  // double-float: value = hi + lo
   float hi, lo;
 };

@@ -84,8 +84,6 @@ __device__ __forceinline__ float gather_dot(const Row<KP>& r, const float* __res
 
 constexpr int kSweepThreads = 256;
 
-// lanes per position in generate: row slices of a multiple of 4 entries
-__host__ __device__ constexpr int gen_lanes(int kp) { return kp % 16 == 0 ? 4 : (kp % 8 == 0 ? 2 : 1); }
 
 // LANES threads share one position: lane h holds entries [h HP, (h+1) HP) of
 // the row (HP = KP / LANES) and the partial sums meet in shuffles.  Each lane
@@ -348,6 +346,12 @@ int launch_whiten(graphgp_graph_t g, graphgp_factor_t f, const float* v, float* 
   }
 
 }  // namespace
+
+int dense_matvec(const float* M, const float* x, float* y, int n0, double* sq, cudaStream_t s) {
+  dense_lower_matvec_kernel<<<(n0 + 7) / 8, 256, 0, s>>>(M, x, y, n0, sq);
+  GGP_CUDA(cudaGetLastError());
+  return GRAPHGP_OK;
+}
 
 int run_generate(graphgp_graph_t g, graphgp_factor_t f, const float* xi, float* v,
                  cudaStream_t s) {

@@ -144,6 +144,10 @@ __device__ __forceinline__ void st_stream_f(float* p, float v, uint64_t pol) {
                : "memory");
 }
 
+// Threads sharing one position in the sweeps: row slices of a multiple of 4
+// entries (KP = padded row length).
+__host__ __device__ constexpr int gen_lanes(int kp) { return kp % 16 == 0 ? 4 : (kp % 8 == 0 ? 2 : 1); }
+
 // Largest grid of kernel `fn` (block threads, dyn smem) that is co-resident.
 template <class F>
 inline int coop_grid(F fn, int threads, size_t smem = 0) {

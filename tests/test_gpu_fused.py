@@ -1,0 +1,87 @@
+"""On-the-fly sweeps (Alg. 1 as printed, no stored factor): bit-identical to
+the stored-factor sweeps, and against the FP64 oracle."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads
+from gpu_util import np_, rel_norm, to_gpu
+
+pytestmark = pytest.mark.gpu
+
+KERNS = [(1, 1.0, 0.1, 1e-6), (0, 1.0, 0.1, 1e-6), (2, 1.3, 0.12, 1e-5), (3, 1.0, 0.05, 1e-4)]
+
+
+def _bits(t):
+    return np_(t).view(np.uint32)
+
+
+@pytest.mark.parametrize("k", [1, 5, 8, 12, 16])
+@pytest.mark.parametrize("kern", KERNS)
+def test_fused_equals_stored_bitwise(gpu_lib, k, kern):
+    N = 20_011
+    pts = workloads.cloud("gaussian", N, 90 + k)
+    g = gpu_lib.build_graph(to_gpu(pts), k, n0=max(k, 64))
+    K = gpu_lib.Kernel(*kern)
+    f = gpu_lib.factor(g, K)
+    xi = to_gpu(workloads.white_noise(N, 91))
+    v = gpu_lib.generate(g, f, xi)
+    vf = gpu_lib.generate_fused(g, K, xi)
+    assert np.array_equal(_bits(vf), _bits(v))
+    ld = torch.zeros(1, dtype=torch.float64, device="cuda")
+    xo = gpu_lib.whiten(g, f, v)
+    xf = gpu_lib.whiten_fused(g, K, v, logdet=ld)
+    assert np.array_equal(_bits(xf), _bits(xo))
+    ld_stored = np_(gpu_lib.logdet(f))[0]
+    assert abs(np_(ld)[0] - ld_stored) <= 1e-12 * abs(ld_stored)
+    n_f = np_(gpu_lib.nll_fused(g, K, v))[0]
+    n_s = np_(gpu_lib.nll(g, f, v))[0]
+    assert abs(n_f - n_s) <= 1e-12 * abs(n_s)
+
+
+def test_fused_against_oracle_tiny(gpu_lib):
+    w = workloads.WORKLOADS["tiny"]
+    pts = workloads.uniform_cube(w["N"], w["seed"])
+    want = oracle.build_graph(pts, w["k"])
+    g = gpu_lib.build_graph(to_gpu(pts), w["k"], n0=want["n0"])
+    kern = w["kernel"]
+    fo = oracle.factor(want["pts_pos"], want["nbr_pos"], w["k"], want["n0"], oracle.Kernel(*kern))
+    xi = workloads.white_noise(w["N"], w["xi_seed"])
+    v = gpu_lib.generate_fused(g, gpu_lib.Kernel(*kern), to_gpu(xi))
+    v_or = oracle.generate(fo, want["nbr_pos"], w["k"], want["n0"], xi.astype(np.float64))
+    assert rel_norm(np_(v), v_or) < 1e-4
+    ld = torch.zeros(1, dtype=torch.float64, device="cuda")
+    v_in = v_or.astype(np.float32)
+    xf = gpu_lib.whiten_fused(g, gpu_lib.Kernel(*kern), to_gpu(v_in), logdet=ld)
+    xi_or = oracle.whiten(fo, want["nbr_pos"], w["k"], want["n0"], v_in.astype(np.float64))
+    assert rel_norm(np_(xf), xi_or) < 1e-4
+    assert abs(np_(ld)[0] - fo["logdet"]) <= 1e-5 * abs(fo["logdet"])
+
+
+def test_fused_large_level_sweep(gpu_lib):
+    """Many depth levels and a cooperative grid far smaller than the levels."""
+    N = 1 << 20
+    pts = workloads.unit_gaussian(N, 92)
+    g = gpu_lib.build_graph(to_gpu(pts), 16)
+    K = gpu_lib.Kernel(1, 1.0, 0.1, 1e-6)
+    f = gpu_lib.factor(g, K)
+    xi = to_gpu(workloads.white_noise(N, 93))
+    assert np.array_equal(_bits(gpu_lib.generate_fused(g, K, xi)), _bits(gpu_lib.generate(g, f, xi)))
+    st, _ = gpu_lib.sync_status(g, f)
+    assert st == 0
+
+
+def test_fused_counts_floored_pivots_and_rejects_large_k(gpu_lib):
+    base = workloads.uniform_cube(1000, 9)
+    pts = np.concatenate([base, base])  # coincident points, no nugget
+    g = gpu_lib.build_graph(to_gpu(pts), 8, n0=64)
+    K = gpu_lib.Kernel(1, 1.0, 0.1, 0.0)
+    f = gpu_lib.factor(g, K)
+    _, bad_stored = gpu_lib.sync_status(g, f)
+    bad = torch.zeros(1, dtype=torch.int64, device="cuda")
+    gpu_lib.whiten_fused(g, K, to_gpu(workloads.white_noise(2000, 1)), not_pd=bad)
+    assert bad_stored > 0 and int(bad.item()) == bad_stored
+    g32 = gpu_lib.build_graph(to_gpu(base), 17, n0=64)
+    with pytest.raises(gpu_lib.GraphGPError):
+        gpu_lib.generate_fused(g32, K, to_gpu(workloads.white_noise(1000, 2)))
