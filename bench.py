@@ -345,6 +345,23 @@ def run_ours(args):
     e2e_ms, e2e_value = replica_rate(s2.elapsed_time(e2), args.steps, N, world, reduce_max)
     assert np.isfinite(v_pin.numpy()).all()
 
+    # on-the-fly sweeps (factors recomputed in the pass, nothing stored)
+    fused = {}
+    if g.k <= 16:
+        def timed(fn, reps=3):
+            fn()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(reps):
+                fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            return a.elapsed_time(b) / reps
+        fused["generate_ms"] = timed(lambda: gg.generate_fused(g, kern, xi, out=v))
+        fused["whiten_ms"] = timed(lambda: gg.whiten_fused(g, kern, v, out=xo, logdet=ld))
+        fused["generate_points_per_s"] = N / (fused["generate_ms"] / 1e3)
+        fused["whiten_points_per_s"] = N / (fused["whiten_ms"] / 1e3)
+
     hbm, peak_kind = _peaks()
     rows = N - g.n0
     bytes_per_point = 8 * k + 16
@@ -374,7 +391,7 @@ def run_ours(args):
                    "whiten_hbm_frac": alg_bytes / (wh_ms / 1e3) / 1e9 / hbm,
                    "graph_build_s": t_graph, "graph_points_per_s": N / t_graph,
                    "factor_s": t_factor, "factor_points_per_s": N / t_factor,
-                   "not_pd_rows": nbad},
+                   "not_pd_rows": nbad, "fused": fused},
         "e2e": {"value": e2e_value, "unit": UNIT, "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": 4 * N, "d2h_bytes_per_step": 8 * N + 8},
         "gpu_launches": 4 * args.steps,
