@@ -79,6 +79,8 @@ def _declare(L):
         "oracle_d2": (ctypes.c_float, [_P, _P]),
         "oracle_knn_brute": (_I, [_P, _P, _I64, _I, _I64, _P]),
         "oracle_knn_tree": (_I, [_P, _P, _P, _I64, _I, _I64, _P]),
+        "oracle_knn_brute_some": (_I, [_P, _P, _P, _I64, _I, _P]),
+        "oracle_factor_rows": (_I, [_P, _P, _P, _I64, _I, _I, _D, _D, _D, _P, _P]),
         "oracle_depth": (_I, [_P, _I64, _I, _I64, _P]),
         "oracle_order": (_I, [_P, _P, _I64, ctypes.c_int32, _P, _P, _P]),
         "oracle_relabel": (_I, [_P, _P, _P, _I64, _I, _I64, _P]),
@@ -158,6 +160,18 @@ def knn_brute(pts, tree_point, k, n0):
     N = pts.shape[0]
     out = np.empty((max(N - n0, 0), k), np.int32)
     _check(lib().oracle_knn_brute(_p(pts), _p(tp), N, k, n0, _p(out)), "knn_brute")
+    return out
+
+
+def knn_brute_some(pts, tree_point, js, k):
+    """The brute-force definition for the tree indices js only: row r holds
+    c(js[r]) nearest first (-1 padding)."""
+    pts = _c(pts, np.float32)
+    tp = _c(tree_point, np.int32)
+    js = _c(js, np.int64)
+    out = np.empty((len(js), k), np.int32)
+    _check(lib().oracle_knn_brute_some(_p(pts), _p(tp), _p(js), len(js), k, _p(out)),
+           "knn_brute_some")
     return out
 
 
@@ -243,6 +257,20 @@ def factor(pts_pos, nbr_pos, k, n0, kern: Kernel):
                                kern.lengthscale, kern.nugget, _p(b), _p(sigma), _p(L0),
                                ctypes.byref(ld), ctypes.byref(bad)), "factor")
     return dict(b=b, sigma=sigma, L0=L0, logdet=ld.value, n_not_pd=bad.value)
+
+
+def factor_rows(pts, idx, nbr, kern: Kernel):
+    """Eq. 2 for the points idx of pts (any order) with neighbour lists nbr
+    (indices into pts, -1 padding): (b [n, k], sigma [n]) in FP64."""
+    pp = _c(pts, np.float32)
+    ix = _c(idx, np.int64)
+    nb = _c(nbr, np.int32)
+    n, k = nb.shape
+    b = np.zeros((n, k), np.float64)
+    sigma = np.empty(n, np.float64)
+    _check(lib().oracle_factor_rows(_p(pp), _p(ix), _p(nb), n, k, kern.type, kern.sigma2,
+                                    kern.lengthscale, kern.nugget, _p(b), _p(sigma)), "factor_rows")
+    return b, sigma
 
 
 def generate(fac, nbr_pos, k, n0, xi):

@@ -205,18 +205,34 @@ static void cand_try(cand_list* c, float d, int32_t idx) {
 
 /* Brute force: the definition.  Row j-n0 of nbr receives the tree indices of
  * c(j) nearest first; rows with fewer than k predecessors are padded with -1. */
+static void knn_brute_one(const float* pts, const int32_t* tree_point, int64_t j, int k,
+                          float* d, int32_t* ix, int32_t* out) {
+  cand_list c = {k, 0, d, ix};
+  const float* q = pts + 3 * (int64_t)tree_point[j];
+  for (int64_t i = 0; i < j; i++)
+    cand_try(&c, oracle_d2(pts + 3 * (int64_t)tree_point[i], q), (int32_t)i);
+  for (int a = 0; a < k; a++) out[a] = a < c.count ? c.i[a] : -1;
+}
+
 int oracle_knn_brute(const float* pts, const int32_t* tree_point, int64_t N,
                      int k, int64_t n0, int32_t* nbr) {
   float* d = (float*)malloc((size_t)k * sizeof(float));
   int32_t* ix = (int32_t*)malloc((size_t)k * sizeof(int32_t));
   if (!d || !ix) { free(d); free(ix); return ORC_ERR; }
-  for (int64_t j = n0; j < N; j++) {
-    cand_list c = {k, 0, d, ix};
-    const float* q = pts + 3 * (int64_t)tree_point[j];
-    for (int64_t i = 0; i < j; i++)
-      cand_try(&c, oracle_d2(pts + 3 * (int64_t)tree_point[i], q), (int32_t)i);
-    for (int a = 0; a < k; a++) nbr[(j - n0) * k + a] = a < c.count ? c.i[a] : -1;
-  }
+  for (int64_t j = n0; j < N; j++) knn_brute_one(pts, tree_point, j, k, d, ix, nbr + (j - n0) * k);
+  free(d);
+  free(ix);
+  return ORC_OK;
+}
+
+/* The same definition for a list of tree indices js[0..n_js) only (sampled
+ * checks of large graphs); row r of nbr receives c(js[r]). */
+int oracle_knn_brute_some(const float* pts, const int32_t* tree_point, const int64_t* js,
+                          int64_t n_js, int k, int32_t* nbr) {
+  float* d = (float*)malloc((size_t)k * sizeof(float));
+  int32_t* ix = (int32_t*)malloc((size_t)k * sizeof(int32_t));
+  if (!d || !ix) { free(d); free(ix); return ORC_ERR; }
+  for (int64_t r = 0; r < n_js; r++) knn_brute_one(pts, tree_point, js[r], k, d, ix, nbr + r * k);
   free(d);
   free(ix);
   return ORC_OK;
@@ -418,6 +434,46 @@ static int row_count(const int32_t* row, int k) {
  * positions 0..n0-1 and sigma_i = L0_ii.  logdet = 2 sum log sigma_i.
  * Distances are FP64 from the FP32 coordinates.                             */
 /* ------------------------------------------------------------------------ */
+/* One conditional (Sec. 2.1 Eq. 2) for point i of pts with neighbour list
+ * row[0..k) (indices into pts, -1 for none): b (k entries, zero past the
+ * list) and sigma.  K, y: k*k and k doubles of scratch.  Returns 1 when a
+ * pivot or sigma^2 was floored. */
+static int factor_row(const float* pts, int64_t i, const int32_t* row, int k, int type, double s2,
+                      double ell, double nug, double* K, double* y, double* b, double* sigma) {
+  double k0 = oracle_kappa(type, s2, ell, 0.0) + nug;
+  int kc = row_count(row, k);
+  const float* xi = pts + 3 * i;
+  for (int a = 0; a < kc; a++) {
+    for (int c = 0; c < kc; c++)
+      K[a * kc + c] = (a == c) ? k0 : oracle_kappa(type, s2, ell, dist64(pts + 3 * (int64_t)row[a], pts + 3 * (int64_t)row[c]));
+    y[a] = oracle_kappa(type, s2, ell, dist64(pts + 3 * (int64_t)row[a], xi));
+  }
+  int clamped = chol_rows(K, kc, kc);
+  solve_lower(K, kc, kc, y);
+  double s = k0;
+  for (int a = 0; a < kc; a++) s -= y[a] * y[a];
+  double floor_v = ORC_PD_FLOOR * k0;
+  if (!(s > floor_v)) { s = floor_v; clamped++; }
+  *sigma = sqrt(s);
+  solve_upper_t(K, kc, kc, y);
+  for (int a = 0; a < k; a++) b[a] = a < kc ? y[a] : 0.0;
+  return clamped ? 1 : 0;
+}
+
+/* factor_row for the points idx[0..n) of pts (any order) with neighbour lists
+ * nbr[r*k .. r*k+k) (indices into pts): sampled checks of large graphs. */
+int oracle_factor_rows(const float* pts, const int64_t* idx, const int32_t* nbr, int64_t n, int k,
+                       int type, double s2, double ell, double nug, double* b, double* sigma) {
+  double* K = (double*)malloc((size_t)k * k * sizeof(double));
+  double* y = (double*)malloc((size_t)k * sizeof(double));
+  if (!K || !y) { free(K); free(y); return ORC_ERR; }
+  for (int64_t r = 0; r < n; r++)
+    factor_row(pts, idx[r], nbr + r * k, k, type, s2, ell, nug, K, y, b + r * k, sigma + r);
+  free(K);
+  free(y);
+  return ORC_OK;
+}
+
 int oracle_factor(const float* pts_pos, const int32_t* nbr_pos, int64_t N,
                   int k, int64_t n0, int type, double s2, double ell,
                   double nug, double* b, double* sigma, double* L0,
@@ -433,26 +489,9 @@ int oracle_factor(const float* pts_pos, const int32_t* nbr_pos, int64_t N,
   double* K = (double*)malloc((size_t)k * k * sizeof(double));
   double* y = (double*)malloc((size_t)k * sizeof(double));
   if (!K || !y) { free(K); free(y); return ORC_ERR; }
-  for (int64_t i = n0; i < N; i++) {
-    const int32_t* row = nbr_pos + (i - n0) * k;
-    int kc = row_count(row, k);
-    const float* xi = pts_pos + 3 * i;
-    for (int a = 0; a < kc; a++) {
-      for (int c = 0; c < kc; c++)
-        K[a * kc + c] = (a == c) ? k0 : oracle_kappa(type, s2, ell, dist64(pts_pos + 3 * (int64_t)row[a], pts_pos + 3 * (int64_t)row[c]));
-      y[a] = oracle_kappa(type, s2, ell, dist64(pts_pos + 3 * (int64_t)row[a], xi));
-    }
-    int clamped = chol_rows(K, kc, kc);
-    solve_lower(K, kc, kc, y);
-    double s = k0;
-    for (int a = 0; a < kc; a++) s -= y[a] * y[a];
-    double floor_v = ORC_PD_FLOOR * k0;
-    if (!(s > floor_v)) { s = floor_v; clamped++; }
-    sigma[i] = sqrt(s);
-    solve_upper_t(K, kc, kc, y);
-    for (int a = 0; a < k; a++) b[(i - n0) * k + a] = a < kc ? y[a] : 0.0;
-    if (clamped) bad++;
-  }
+  for (int64_t i = n0; i < N; i++)
+    bad += factor_row(pts_pos, i, nbr_pos + (i - n0) * k, k, type, s2, ell, nug, K, y,
+                      b + (i - n0) * k, sigma + i);
   free(K);
   free(y);
   double ld = 0.0;

@@ -228,7 +228,8 @@ __global__ void __launch_bounds__(128) factor_backward_kernel(
     const float4* __restrict__ xs, const int32_t* __restrict__ nbr, int64_t N, int k, int kp,
     int64_t n0, KernF kf, int mode, const float* __restrict__ coef, float beta,
     const float* __restrict__ v, const float* __restrict__ xi, float* __restrict__ xibar_out,
-    double* __restrict__ thetabar) {
+    double* __restrict__ thetabar, int64_t* __restrict__ rescue_rows,
+    unsigned long long* __restrict__ rescue_count) {
   constexpr int PPW = 32 / G;
   constexpr int GS = PFLayout<G>::GS;
   __shared__ __align__(16) float Ls[4 * PPW * GS];
@@ -295,12 +296,47 @@ __global__ void __launch_bounds__(128) factor_backward_kernel(
       ps += __shfl_xor_sync(full, ps, o, G);
       pn += __shfl_xor_sync(full, pn, o, G);
     }
+    // rows the forward factor recomputed in FP64 (rescue.cuh): the FP32 sums
+    // above are discarded and the row goes to factor_backward_rescue_kernel
+    const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (grp * G));
+    const bool lane_bad = real && !isfinite(st.b_own);
+    const bool rescue = st.clamped || !(st.min_piv >= kRescuePivot * (kf.s2 + kf.nug)) ||
+                        !isfinite(st.sigma) || (__ballot_sync(full, lane_bad) & gmask);
     if (valid && a == 0) {
-      tl += pl;
-      ts += ps;
-      tn += pn;
-      if (mode == 1) xibar_out[i] = sigma * ci;
+      if (rescue) {
+        rescue_rows[atomicAdd(rescue_count, 1ull)] = i;
+      } else {
+        tl += pl;
+        ts += ps;
+        tn += pn;
+        if (mode == 1) xibar_out[i] = sigma * ci;
+      }
     }
+  }
+  block_add3(tl, ts, tn, thetabar);
+}
+
+// FP64 backward of the rows the lane-group kernel handed over (rescue.cuh).
+template <int G, int KT>
+__global__ void __launch_bounds__(128) factor_backward_rescue_kernel(
+    const float4* __restrict__ xs, const int32_t* __restrict__ nbr, int k, int kp, int64_t n0,
+    KernF kf, int mode, const float* __restrict__ coef, float beta, const float* __restrict__ v,
+    const float* __restrict__ xi, float* __restrict__ xibar_out, double* __restrict__ thetabar,
+    const int64_t* __restrict__ rows, const unsigned long long* __restrict__ count) {
+  double tl = 0.0, ts = 0.0, tn = 0.0;
+  const int64_t n = (int64_t)*count;
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = rows[r];
+    const int32_t* row_ptr = nbr + (i - n0) * kp;
+    Row64<G> R;
+    row_factor64<G, KT>(R, xs, row_ptr, k, xs[i], kf);
+    const float sg = (float)R.sigma;
+    const float ci = coef[i];
+    const double al = mode == 0 ? -(double)ci / sg : (double)ci;
+    const double sb = al * (double)xi[i] + (double)beta / sg;
+    row_backward64<G, KT>(R, xs, row_ptr, k, xs[i], kf, v, al, sb, sg, tl, ts, tn);
+    if (mode == 1) xibar_out[i] = sg * ci;
   }
   block_add3(tl, ts, tn, thetabar);
 }
@@ -323,7 +359,8 @@ __global__ void __launch_bounds__(128) factor_backward_thread_kernel(
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < npts;
        t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = n0 + t;
-    const int4* row = reinterpret_cast<const int4*>(nbr + t * K);
+    const int32_t* row_ptr = nbr + t * K;
+    const int4* row = reinterpret_cast<const int4*>(row_ptr);
     const float4 xq = __ldg(xs + i);
     PointRegs<K> p;
     {
@@ -337,6 +374,17 @@ __global__ void __launch_bounds__(128) factor_backward_thread_kernel(
         x[4 * q + 3] = __ldg(xs + c.w);
       }
       point_factor_thread<K, KT>(p, k, kf, x, xq);
+    }
+    if (needs_rescue(p, k, kf)) {
+      Row64<K> R;
+      row_factor64<K, KT>(R, xs, row_ptr, k, xq, kf);
+      const float sg = (float)R.sigma;
+      const float ci = coef[i];
+      const double alpha = mode == 0 ? -(double)ci / sg : (double)ci;
+      const double sigbar = alpha * (double)xi[i] + (double)beta / sg;
+      row_backward64<K, KT>(R, xs, row_ptr, k, xq, kf, v, alpha, sigbar, sg, tl, ts, tn);
+      if (mode == 1) xibar_out[i] = sg * ci;
+      continue;
     }
     const float sigma = p.sigma;
     const float ci = coef[i];
@@ -405,10 +453,19 @@ int launch_factor_backward(graphgp_graph_t g, graphgp_factor_t f, int mode, cons
   constexpr int PPW = 32 / G;
   unsigned grid = grid_for((npts + 4 * PPW - 1) / (4 * PPW) * 128, 128, 16);
   KernF kf = make_kernf(f->kern);
+  Scratch sc(s);
+  int64_t* rows = nullptr;
+  unsigned long long* cnt = nullptr;
+  GGP_TRY(sc.alloc(&rows, npts));
+  GGP_TRY(sc.alloc(&cnt, 1));
+  GGP_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), s));
+  const unsigned rgrid = (unsigned)num_sms() * 2;
 #define GGP_FB(KT)                                                                          \
   factor_backward_kernel<G, KT><<<grid, 128, 0, s>>>(g->xs, g->nbr, g->N, g->k, g->kp, g->n0, \
                                                      kf, mode, coef, beta, v, xi, xibar,     \
-                                                     thetabar)
+                                                     thetabar, rows, cnt);                   \
+  factor_backward_rescue_kernel<G, KT><<<rgrid, 128, 0, s>>>(                               \
+      g->xs, g->nbr, g->k, g->kp, g->n0, kf, mode, coef, beta, v, xi, xibar, thetabar, rows, cnt)
   switch (f->kern.type) {
     case GRAPHGP_MATERN12: GGP_FB(GRAPHGP_MATERN12); break;
     case GRAPHGP_MATERN32: GGP_FB(GRAPHGP_MATERN32); break;

@@ -167,6 +167,7 @@ namespace ggp {
 // ---------------------------------------------------------------------------
 struct KernF {
   float s2, inv_ell, nug;
+  double s2d, elld, nugd;  // the same parameters in FP64 (rescue path)
 };
 
 template <int KT>
@@ -217,6 +218,9 @@ inline KernF make_kernf(const graphgp_kernel& k) {
   p.s2 = (float)k.sigma2;
   p.inv_ell = (float)(1.0 / k.lengthscale);
   p.nug = (float)k.nugget;
+  p.s2d = k.sigma2;
+  p.elld = k.lengthscale;
+  p.nugd = k.nugget;
   return p;
 }
 

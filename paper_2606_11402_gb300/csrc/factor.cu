@@ -46,12 +46,29 @@ __global__ void __launch_bounds__(128) point_factor_kernel(
     PointState<G> st;
     point_factor_group<G, KT>(st, a, k, kf, xs[ca], xs[i], Lg);
     __syncwarp();
+    // rescue decision, uniform over the group's lanes
+    const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (grp * G));
+    const bool lane_bad = a < k && !isfinite(st.b_own);
+    const bool rescue = st.clamped || !(st.min_piv >= kRescuePivot * (kf.s2 + kf.nug)) ||
+                        !isfinite(st.sigma) || (__ballot_sync(0xffffffffu, lane_bad) & gmask);
     if (valid) {
-      if (a < kp) b_out[(i - n0) * kp + a] = a < k ? st.b_own : 0.0f;
-      if (a == 0) {
-        sigma_out[i] = st.sigma;
-        acc.mul(st.sigma);
-        if (st.clamped) clamped_rows++;
+      if (rescue) {
+        if (a == 0) {
+          Row64<G> R;
+          row_factor64<G, KT>(R, xs, nbr + (i - n0) * kp, k, xs[i], kf);
+          for (int e = 0; e < kp; e++) b_out[(i - n0) * kp + e] = e < k ? (float)R.b[e] : 0.0f;
+          const float sg = (float)R.sigma;
+          sigma_out[i] = sg;
+          acc.mul(sg);
+          if (R.clamped) clamped_rows++;
+        }
+      } else {
+        if (a < kp) b_out[(i - n0) * kp + a] = a < k ? st.b_own : 0.0f;
+        if (a == 0) {
+          sigma_out[i] = st.sigma;
+          acc.mul(st.sigma);
+          if (st.clamped) clamped_rows++;
+        }
       }
     }
   }
@@ -87,7 +104,9 @@ __global__ void __launch_bounds__(128) point_factor_thread_kernel(
       x[4 * q + 3] = __ldg(xs + c.w);
     }
     PointRegs<K> p;
-    point_factor_thread<K, KT>(p, k, kf, x, __ldg(xs + i));
+    const float4 xq = __ldg(xs + i);
+    point_factor_thread<K, KT>(p, k, kf, x, xq);
+    if (needs_rescue(p, k, kf)) rescue_thread<K, KT>(p, xs, nbr + t * K, k, xq, kf);
     float4* bo = reinterpret_cast<float4*>(b_out + t * K);
 #pragma unroll
     for (int q = 0; q < K / 4; q++)

@@ -5,8 +5,9 @@
 // of 2k + 5 with stored weights); this is the form for kernel parameters that
 // change at every step.
 //
-// Each thread owns one point and runs point_factor_thread (k <= 16), whose b
-// and sigma are bit-identical to the stored factor's; the dot b . v_c then
+// Each thread owns one point and runs point_factor_thread (k <= 16) with the
+// same FP64 rescue decision as the factor kernel, so b and sigma are
+// bit-identical to the stored factor's; the dot b . v_c then
 // follows the stored sweeps' summation order (the row cut into gen_lanes(K)
 // slices, two alternating accumulators per slice, slices combined as their
 // xor-shuffle tree does), so the fused sweeps return the same bits as
@@ -59,16 +60,20 @@ __device__ __forceinline__ float dot_stored_order(const float (&b)[K], const int
 template <int K, int KT>
 __device__ __forceinline__ void factor_at(PointRegs<K>& p, const float4* __restrict__ xs,
                                           const int32_t* row, int64_t i, int k, const KernF& kf) {
-  float4 x[K];
+  const float4 xq = __ldg(xs + i);
+  {
+    float4 x[K];
 #pragma unroll
-  for (int q = 0; q < K / 4; q++) {
-    const int4 c = __ldg(reinterpret_cast<const int4*>(row) + q);
-    x[4 * q] = __ldg(xs + c.x);
-    x[4 * q + 1] = __ldg(xs + c.y);
-    x[4 * q + 2] = __ldg(xs + c.z);
-    x[4 * q + 3] = __ldg(xs + c.w);
+    for (int q = 0; q < K / 4; q++) {
+      const int4 c = __ldg(reinterpret_cast<const int4*>(row) + q);
+      x[4 * q] = __ldg(xs + c.x);
+      x[4 * q + 1] = __ldg(xs + c.y);
+      x[4 * q + 2] = __ldg(xs + c.z);
+      x[4 * q + 3] = __ldg(xs + c.w);
+    }
+    point_factor_thread<K, KT>(p, k, kf, x, xq);
   }
-  point_factor_thread<K, KT>(p, k, kf, x, __ldg(xs + i));
+  if (needs_rescue(p, k, kf)) rescue_thread<K, KT>(p, xs, row, k, xq, kf);
 }
 
 __device__ inline void block_add_count(unsigned long long c, unsigned long long* out) {

@@ -16,6 +16,7 @@
 #include <type_traits>
 
 #include "common.cuh"
+#include "rescue.cuh"
 
 namespace ggp {
 
@@ -75,6 +76,7 @@ struct PointState {
   float b_own;     // b_a
   float sigma;     // conditional standard deviation (same on all lanes)
   bool clamped;    // a pivot was floored (same on all lanes)
+  float min_piv;   // smallest pivot before flooring (same on all lanes)
 };
 
 // Shared-memory row stride and per-group footprint (floats) for G lanes.
@@ -109,6 +111,7 @@ __device__ __forceinline__ void point_factor_group(PointState<G>& st, int a, int
   const float diag = real ? k0 : 1.0f;
   DF s2{k0, 0.0f};
   st.clamped = false;
+  st.min_piv = k0;
   st.inv_own = 1.0f;
   st.y_own = 0.0f;
 #pragma unroll
@@ -129,6 +132,7 @@ __device__ __forceinline__ void point_factor_group(PointState<G>& st, int a, int
     tv += t2;
     float piv = __shfl_sync(full, tv, j, G);
     float pfloor = kPdFloor * __shfl_sync(full, diag, j, G);
+    st.min_piv = fminf(st.min_piv, piv);
     if (!(piv > pfloor)) {
       piv = pfloor;
       st.clamped = true;
@@ -218,6 +222,7 @@ struct PointRegs {
   float y[K];                // y = L^-1 K_ci, then b = L^-T y (zero for a >= k)
   float sigma;
   bool clamped;
+  float min_piv;             // smallest pivot before flooring
   // 1 / L_jj, recomputed where needed (the same correctly rounded quotient)
   __device__ __forceinline__ float inv(int j) const { return 1.0f / L[tri(j, j)]; }
 };
@@ -255,10 +260,12 @@ __device__ __forceinline__ void point_factor_thread(PointRegs<K>& p, int k, cons
   });
   DF s2{k0, 0.0f};
   bool clamped = false;
+  float min_piv = k0;
   const float pfloor = kPdFloor * k0;
   static_for<0, K>([&](auto Jc) {
     constexpr int j = decltype(Jc)::value;
     float piv = schur_value<K, j, j>(p);
+    min_piv = fminf(min_piv, piv);
     if (!(piv > pfloor)) {
       piv = pfloor;
       clamped = true;
@@ -282,6 +289,7 @@ __device__ __forceinline__ void point_factor_thread(PointRegs<K>& p, int k, cons
     clamped = true;
   }
   p.clamped = clamped;
+  p.min_piv = min_piv;
   p.sigma = sqrtf(sig2);
   // b = L^-T y, last entry first
   static_for<0, K>([&](auto Jr) {
@@ -311,6 +319,31 @@ __device__ __forceinline__ void thread_chol_solve(const PointRegs<K>& p, float (
 #pragma unroll
     for (int a = 0; a < j; a++) r[a] = fmaf(-p.L[tri(j, a)], gj, r[a]);
   });
+}
+
+// Whether a conditional computed in FP32 must be recomputed in FP64 (see
+// rescue.cuh): a floored pivot or sigma^2, a pivot below kRescuePivot of the
+// diagonal, or a non-finite weight or sigma.
+template <int K>
+__device__ __forceinline__ bool needs_rescue(const PointRegs<K>& p, int k, const KernF& kf) {
+  bool bad = p.clamped || !(p.min_piv >= kRescuePivot * (kf.s2 + kf.nug)) || !isfinite(p.sigma);
+#pragma unroll
+  for (int a = 0; a < K; a++) bad |= !isfinite(p.y[a]);
+  return bad;
+}
+
+// The FP64 conditional of the row in place of the FP32 one: b (zero past k),
+// sigma and the floor flag, rounded to FP32.
+template <int K, int KT>
+__device__ __forceinline__ void rescue_thread(PointRegs<K>& p, const float4* __restrict__ xs,
+                                              const int32_t* row, int k, float4 xq,
+                                              const KernF& kf) {
+  Row64<K> R;
+  row_factor64<K, KT>(R, xs, row, k, xq, kf);
+#pragma unroll
+  for (int a = 0; a < K; a++) p.y[a] = a < k ? (float)R.b[a] : 0.0f;
+  p.sigma = (float)R.sigma;
+  p.clamped = R.clamped;
 }
 
 }  // namespace ggp

@@ -1,0 +1,158 @@
+// FP64 rescue of single conditionals (Sec. 2.1 Eq. 2).
+//
+// The per-point factors run in FP32.  Their error grows like cond(K_cc) 2^-24,
+// and when neighbours nearly coincide on the scale of the lengthscale (the
+// large-dynamic-range cloud without nugget has cond(K_cc) up to 1e11) the
+// FP32 Cholesky keeps positive pivots but its backward solve overflows: b is
+// no longer finite.  A row whose FP32 factor floored a pivot or sigma^2, whose
+// smallest pivot fell below kRescuePivot of the diagonal, or whose b or sigma
+// is not finite is recomputed here in FP64 from the FP32 coordinates: kernel
+// values from FP64 distances, Cholesky by rows, forward and backward solves,
+// sigma^2 = K_ii - y.y, with the same pivot floor (1e-7 of the diagonal).
+// Every kernel that evaluates a conditional (factor, on-the-fly sweeps,
+// factor backward) takes the same decision on the same FP32 values and calls
+// the same code, so stored and recomputed factors agree.  On the measured
+// workloads with a nugget no row needs it.
+#pragma once
+
+#include "common.cuh"
+
+namespace ggp {
+
+constexpr float kRescuePivot = 1e-6f;
+constexpr double kPdFloor64 = 1e-7;
+
+__host__ __device__ constexpr int tri64(int a, int c) { return a * (a + 1) / 2 + c; }
+
+template <int KT>
+__device__ __forceinline__ double kappa64(const KernF& p, double r) {
+  const double s2 = p.s2d, l = p.elld;
+  if (KT == GRAPHGP_SQEXP) return s2 * exp(-0.5 * (r / l) * (r / l));
+  if (KT == GRAPHGP_MATERN12) return s2 * exp(-r / l);
+  if (KT == GRAPHGP_MATERN32) {
+    const double a = 1.7320508075688772 * r / l;
+    return s2 * (1.0 + a) * exp(-a);
+  }
+  const double a = 2.2360679774997896 * r / l;
+  return s2 * (1.0 + a + a * a / 3.0) * exp(-a);
+}
+
+template <int KT>
+__device__ __forceinline__ double dkappa64_dell(const KernF& p, double r) {
+  const double s2 = p.s2d, l = p.elld;
+  if (KT == GRAPHGP_SQEXP) return s2 * exp(-0.5 * (r / l) * (r / l)) * r * r / (l * l * l);
+  if (KT == GRAPHGP_MATERN12) return s2 * exp(-r / l) * r / (l * l);
+  if (KT == GRAPHGP_MATERN32) {
+    const double a = 1.7320508075688772 * r / l;
+    return s2 * a * a * exp(-a) / l;
+  }
+  const double a = 2.2360679774997896 * r / l;
+  return s2 * a * a * (1.0 + a) * exp(-a) / (3.0 * l);
+}
+
+__device__ __forceinline__ double dist64(float4 a, float4 b) {
+  const double dx = (double)a.x - (double)b.x, dy = (double)a.y - (double)b.y,
+               dz = (double)a.z - (double)b.z;
+  return sqrt(dx * dx + dy * dy + dz * dz);
+}
+
+// Row state of the FP64 conditional: L (packed lower), b, sigma.
+template <int KMAX>
+struct Row64 {
+  double L[KMAX * (KMAX + 1) / 2];
+  double b[KMAX];
+  double sigma;
+  bool clamped;
+};
+
+// Factor of the row with neighbours row[0..k) (indices into xs) and point xq.
+template <int KMAX, int KT>
+__device__ __noinline__ void row_factor64(Row64<KMAX>& R, const float4* __restrict__ xs,
+                                          const int32_t* row, int k, float4 xq, const KernF& p) {
+  const double k0 = kappa64<KT>(p, 0.0) + p.nugd;
+  R.clamped = false;
+  for (int i = 0; i < k; i++) {
+    const float4 xi = __ldg(xs + row[i]);
+    for (int j = 0; j <= i; j++) {
+      double s = (i == j) ? k0 : kappa64<KT>(p, dist64(xi, __ldg(xs + row[j])));
+      for (int m = 0; m < j; m++) s -= R.L[tri64(i, m)] * R.L[tri64(j, m)];
+      if (i == j) {
+        const double fl = kPdFloor64 * k0;
+        if (!(s > fl)) {
+          s = fl;
+          R.clamped = true;
+        }
+        R.L[tri64(i, i)] = sqrt(s);
+      } else {
+        R.L[tri64(i, j)] = s / R.L[tri64(j, j)];
+      }
+    }
+    R.b[i] = kappa64<KT>(p, dist64(xi, xq));
+  }
+  // y = L^-1 K_ci, sigma^2 = K_ii - y.y, b = L^-T y
+  for (int i = 0; i < k; i++) {
+    double s = R.b[i];
+    for (int m = 0; m < i; m++) s -= R.L[tri64(i, m)] * R.b[m];
+    R.b[i] = s / R.L[tri64(i, i)];
+  }
+  double s2 = k0;
+  for (int i = 0; i < k; i++) s2 -= R.b[i] * R.b[i];
+  if (!(s2 > kPdFloor64 * k0)) {
+    s2 = kPdFloor64 * k0;
+    R.clamped = true;
+  }
+  R.sigma = sqrt(s2);
+  for (int i = k - 1; i >= 0; i--) {
+    double s = R.b[i];
+    for (int m = i + 1; m < k; m++) s -= R.L[tri64(m, i)] * R.b[m];
+    R.b[i] = s / R.L[tri64(i, i)];
+  }
+}
+
+// The row's contribution to thetabar = (d/dl, d/dsigma2, d/dnugget) from the
+// cotangents of its weights, bbar_a = alpha v_c(a), and of its conditional
+// standard deviation, sigbar (Sec. 2.3; with s = sigma^2, g = K_cc^-1 bbar:
+// Kbar_cc = -g b^T + sbar b b^T, Kbar_ci = g - 2 sbar b, Kbar_ii = sbar).
+// R holds the row's factor; sigma is the FP32 value the sweeps used.
+template <int KMAX, int KT>
+__device__ __noinline__ void row_backward64(const Row64<KMAX>& R, const float4* __restrict__ xs,
+                                            const int32_t* row, int k, float4 xq, const KernF& p,
+                                            const float* __restrict__ v, double alpha,
+                                            double sigbar, double sigma, double& tl, double& ts,
+                                            double& tn) {
+  double g[KMAX];
+  const double sbar = sigbar / (2.0 * sigma);
+  for (int i = 0; i < k; i++) g[i] = alpha * (double)v[row[i]];
+  for (int i = 0; i < k; i++) {
+    double s = g[i];
+    for (int m = 0; m < i; m++) s -= R.L[tri64(i, m)] * g[m];
+    g[i] = s / R.L[tri64(i, i)];
+  }
+  for (int i = k - 1; i >= 0; i--) {
+    double s = g[i];
+    for (int m = i + 1; m < k; m++) s -= R.L[tri64(m, i)] * g[m];
+    g[i] = s / R.L[tri64(i, i)];
+  }
+  double pl = 0.0, ps = sbar, pn = sbar;  // Kbar_ii = sbar
+  for (int a = 0; a < k; a++) {
+    const float4 xa = __ldg(xs + row[a]);
+    const double kaa = -g[a] * R.b[a] + sbar * R.b[a] * R.b[a];
+    ps += kaa;
+    pn += kaa;
+    for (int c = 0; c < a; c++) {
+      const double kb = (-g[a] * R.b[c] + sbar * R.b[a] * R.b[c]) + (-g[c] * R.b[a] + sbar * R.b[c] * R.b[a]);
+      const double r = dist64(xa, __ldg(xs + row[c]));
+      ps += kb * kappa64<KT>(p, r) / p.s2d;
+      pl += kb * dkappa64_dell<KT>(p, r);
+    }
+    const double kci = g[a] - 2.0 * sbar * R.b[a];
+    const double r = dist64(xa, xq);
+    ps += kci * kappa64<KT>(p, r) / p.s2d;
+    pl += kci * dkappa64_dell<KT>(p, r);
+  }
+  tl += pl;
+  ts += ps;
+  tn += pn;
+}
+
+}  // namespace ggp

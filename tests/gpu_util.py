@@ -69,3 +69,18 @@ def fp32_tolerance(want, kern, rows=300, base=1e-4):
         worst_s = max(worst_s, cond * K[k, k] / max(s2, 1e-300))
     eps = 2.0 ** -24
     return max(base, 8 * worst_b * eps), max(base, 8 * worst_s * eps)
+
+
+def row_tolerance(xc, xq, kern, base=1e-4):
+    """fp32_tolerance's bound for one conditional: neighbours xc [k, 3], point
+    xq [3]."""
+    x = np.vstack([np.asarray(xc, np.float64), np.asarray(xq, np.float64)[None]])
+    k = len(xc)
+    r = np.sqrt(((x[:, None] - x[None]) ** 2).sum(-1))
+    K = _kappa_np(kern, r) + kern[3] * np.eye(k + 1)
+    Kc = K[:k, :k]
+    cond = np.linalg.cond(Kc)
+    b = np.linalg.solve(Kc, K[:k, k])
+    s2 = K[k, k] - K[k, :k] @ b
+    eps = 2.0 ** -24
+    return max(base, 8 * cond * eps), max(base, 8 * cond * K[k, k] / max(s2, 1e-300) * eps)

@@ -108,6 +108,36 @@ def test_all_dense(gpu_lib):
     assert rel_norm(v, oracle.generate(fo, want["nbr_pos"], 8, 300, xi.astype(np.float64))) < 1e-4
 
 
+@pytest.mark.parametrize("k", [16, 32])
+def test_fp64_rescue_of_ill_conditioned_rows(gpu_lib, k):
+    """Large-dynamic-range cloud without nugget (cond(K_cc) up to ~1e11): rows
+    whose FP32 factor floors a pivot or loses its accuracy are recomputed in
+    FP64, so the factor stays finite, the floored rows are those of the FP64
+    oracle, and the sweeps and gradients follow the oracle."""
+    N = 20_011
+    pts = workloads.ldr_cloud(N, 33)
+    kern = (1, 1.0, 0.05, 0.0)
+    g, f, want, fo, = _setup(gpu_lib, pts, k, kern, n0=256)
+    b, sigma, _ = (np_(t) for t in f.export())
+    assert np.isfinite(b).all() and np.isfinite(sigma).all()
+    st, bad = gpu_lib.sync_status(g, f)
+    assert fo["n_not_pd"] > 0 and abs(bad - fo["n_not_pd"]) <= 0.01 * fo["n_not_pd"], (bad, fo["n_not_pd"])
+    tol = fp32_tolerance(want, kern)
+    assert rel_norm(b, fo["b"]) < tol[0]
+    xi = workloads.white_noise(N, 34)
+    v = np_(gpu_lib.generate(g, f, to_gpu(xi)))
+    assert np.isfinite(v).all()
+    assert rel_norm(v, oracle.generate(fo, want["nbr_pos"], k, 256, xi.astype(np.float64))) < tol[0]
+    if k <= 16:
+        vf = np_(gpu_lib.generate_fused(g, gpu_lib.Kernel(*kern), to_gpu(xi)))
+        assert np.array_equal(vf.view(np.uint32), v.view(np.uint32))
+    vbar, tb = gpu_lib.nll_backward(g, f, to_gpu(v))
+    assert np.isfinite(np_(vbar)).all() and np.isfinite(np_(tb)).all()
+    _, tb_or = oracle.nll_grad(want, oracle.Kernel(*kern), v.astype(np.float64))
+    scale = np.max(np.abs(tb_or))
+    assert np.all(np.abs(np_(tb) - tb_or) <= max(2e-3, 20 * tol[1]) * scale), (np_(tb), tb_or)
+
+
 @pytest.mark.parametrize("d", [1, 2])
 def test_factor_and_sweeps_lower_dimensions(gpu_lib, d):
     """A 2-D (1-D) cloud: factor, generate and whiten against the oracle on the
