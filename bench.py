@@ -196,15 +196,24 @@ def serving_bench(n_inst=64, rate=2000.0, duration=5.0, seed=8, n_slots=8):
             server.wait(t)
     sv.run_stream(warm, inputs, server=server)
     eng = sv.run_stream(reqs, inputs, server=server)
+    # saturation: 2000 requests arriving within 1 ms, completion rate
+    burst = sv.poisson_stream(n_inst, 2.0e6, 1.0e-3, seed + 3)
+    eng_sat = sv.run_stream(burst, inputs, server=server)
     server.close()
     sv.run_stream(warm, inputs, instances=inst)
     one = sv.run_stream(reqs, inputs, instances=inst)
+    one_sat = sv.run_stream(burst, inputs, instances=inst)
     pts_req = float(np.mean([inst[r.inst][0].N for r in reqs])) if reqs else 0.0
     return {"workload": (f"Poisson {rate:.0f} req/s for {duration:.0f} s over {n_inst} resident "
                          "instances (N log-uniform 1e3..1e6, k in {8,16,32}, Matern-3/2 "
                          "l log-uniform 0.01..0.2, uniform/clustered), ops uniform over "
                          "generate/whiten/logdet/nll-gradient"),
             "engine": eng, "one_at_a_time": one, "slots": n_slots,
+            "saturation": {"requests": len(burst),
+                           "engine_rps": eng_sat["throughput_rps"],
+                           "one_at_a_time_rps": one_sat["throughput_rps"],
+                           "engine_p99_ms": eng_sat["p99_ms"],
+                           "one_at_a_time_p99_ms": one_sat["p99_ms"]},
             "mean_points_per_request": pts_req, "setup_s": t_setup,
             "instances_points": total_pts}
 
