@@ -5,15 +5,15 @@
 // (Sec. 2.2: points of one depth level are conditionally independent)
 // v_i = b_i . v_c(i) + sigma_i xi_i; every neighbour lies in an earlier level.
 // One cooperative launch walks all levels with a grid-wide barrier between
-// consecutive levels (sweepsync.cuh); each thread loads the neighbour row,
-// weights, sigma and xi of its next point before waiting, so the row stream
-// overlaps the barrier and only the gathers of v wait for it.
+// consecutive levels (sweepsync.cuh).  Rows, sigma and xi do not depend on
+// the field: each lane group loads those of its next step before gathering
+// the current one, and those of a level's first step before the barrier, so
+// the row stream overlaps both the gathers and the barrier.
 //
-// whiten: xi_i = (v_i - b_i . v_c(i)) / sigma_i has no dependencies; one
-// streaming launch in position order (plus xi_0 = L0^-1 v_0 for the dense
-// block).  Positions are level-major and spatially sorted inside a level, and
-// neighbours sit a few levels back, so the gathered v lines stay in L2 when
-// the row stream is marked evict-first and v evict-last.
+// whiten: xi_i = (v_i - b_i . v_c(i)) / sigma_i has no dependencies.  Blocks
+// walk spatial tiles through every level (plus xi_0 = L0^-1 v_0 for the
+// dense block), so the gathered v lines of a tile stay in L1; rows are
+// streamed without L1 allocation, v is kept in L2 (evict-last).
 #include <algorithm>
 
 #include "sweepsync.cuh"
@@ -58,6 +58,22 @@ __device__ __forceinline__ void load_row(Row<KP>& r, const int32_t* __restrict__
   }
 }
 
+
+// The same row, loaded without allocating in L1 (the whiten sweep keeps L1
+// for the gathered field values of its tile).
+template <int KP>
+__device__ __forceinline__ void load_row_na(Row<KP>& r, const int32_t* __restrict__ nbr,
+                                            const float* __restrict__ b, int64_t row,
+                                            uint64_t pol) {
+  const int4* np = reinterpret_cast<const int4*>(nbr + row * KP);
+  const float4* bp = reinterpret_cast<const float4*>(b + row * KP);
+#pragma unroll
+  for (int q = 0; q < KP / 4; q++) {
+    r.n[q] = ld_stream_na_i4(np + q, pol);
+    r.w[q] = ld_stream_na_f4(bp + q, pol);
+  }
+}
+
 // sum_a b_a v[c_a].  LEVEL: v is written level by level in the same launch;
 // the gathered entries belong to earlier levels, published by the barrier.
 template <int KP, bool LEVEL>
@@ -85,19 +101,24 @@ __device__ __forceinline__ float gather_dot(const Row<KP>& r, const float* __res
 constexpr int kSweepThreads = 256;
 
 
+// Positions per lane group and step of generate_kernel: as many as keep the
+// two row buffers below about 64 registers.
+__host__ __device__ constexpr int gen_steps(int hp) { return hp <= 4 ? 4 : (hp <= 8 ? 2 : 1); }
+
 // LANES threads share one position: lane h holds entries [h HP, (h+1) HP) of
-// the row (HP = KP / LANES) and the partial sums meet in shuffles.  Each lane
-// loads the row of its next position before gathering the current one, so a
-// row load is always in flight under the gathers.
-template <int KP, int LANES>
+// the row (HP = KP / LANES) and the partial sums meet in shuffles.  A lane
+// group takes U positions per step, and the rows, sigma and xi of its next
+// step are loaded before the gathers of the current one, so their DRAM
+// latency hides under the gathers.  The first step of a level is loaded
+// before the level barrier (rows do not depend on the field).
+template <int KP, int LANES, int U>
 __global__ void __launch_bounds__(kSweepThreads) generate_kernel(
     const int32_t* __restrict__ nbr, const float* __restrict__ b, const float* __restrict__ sigma,
     const float* __restrict__ xi, float* v, const int64_t* __restrict__ level_off,
     int num_levels, int64_t n0, LevelBarrier lb) {
-  constexpr int HP = KP / LANES;              // row entries per lane
-  constexpr int GPB = kSweepThreads / LANES;  // lane groups per block
-  constexpr int U = 2;                        // positions per lane group per step
-  constexpr int PPB = U * GPB;                // positions per block step
+  constexpr int HP = KP / LANES;                // row entries per lane
+  constexpr int GPB = kSweepThreads / LANES;    // lane groups per block
+  constexpr int PPB = U * GPB;                  // positions per block step
   __shared__ int s_flag;
   const uint64_t pol_rows = l2_evict_first();
   const uint64_t pol_v = l2_evict_last();
@@ -105,52 +126,61 @@ __global__ void __launch_bounds__(kSweepThreads) generate_kernel(
   const int slot = threadIdx.x / LANES;
   const int32_t* nb = nbr + h * HP;
   const float* bw = b + h * HP;
+  Row<HP> rn[U];
+  float sgn[U], xn[U];
   for (int l = 1; l < num_levels; l++) {
-    // each block takes one contiguous, spatially compact slice of the level
     const int64_t lo = level_off[l], n = level_off[l + 1] - lo;
     const int64_t per = (n + gridDim.x - 1) / gridDim.x;
     const int64_t b0 = lo + min((int64_t)blockIdx.x * per, n);
     const int64_t hi = lo + min((int64_t)(blockIdx.x + 1) * per, n);
-    int64_t p = b0 + slot;  // positions p + u GPB, u < U
-    Row<HP> r[U];
-    float sg[U], x[U];
+    int64_t p = b0 + slot;
 #pragma unroll
     for (int u = 0; u < U; u++) {
       const int64_t q = p + u * GPB;
-      sg[u] = x[u] = 0.0f;
+      sgn[u] = xn[u] = 0.0f;
       if (q < hi) {
-        load_row<HP>(r[u], nb, bw, (q - n0) * LANES, pol_rows);
+        load_row<HP>(rn[u], nb, bw, (q - n0) * LANES, pol_rows);
         if (h == 0) {
-          sg[u] = ld_stream_f(sigma + q, pol_rows);
-          x[u] = ld_stream_f(xi + q, pol_rows);
+          sgn[u] = ld_stream_f(sigma + q, pol_rows);
+          xn[u] = ld_stream_f(xi + q, pol_rows);
         }
       }
     }
     if (l > 1 && lb.wait(l - 1, gridDim.x, &s_flag)) return;
-    // every lane of a warp runs the same number of steps (shuffles below)
     const int64_t steps = (hi - b0 + PPB - 1) / PPB;
     for (int64_t st = 0; st < steps; st++) {
+      Row<HP> r[U];
+      float sg[U], x[U];
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        r[u] = rn[u];
+        sg[u] = sgn[u];
+        x[u] = xn[u];
+      }
+      const int64_t pn = p + PPB;
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        const int64_t qn = pn + u * GPB;
+        if (qn < hi) {
+          load_row<HP>(rn[u], nb, bw, (qn - n0) * LANES, pol_rows);
+          if (h == 0) {
+            sgn[u] = ld_stream_f(sigma + qn, pol_rows);
+            xn[u] = ld_stream_f(xi + qn, pol_rows);
+          }
+        }
+      }
       float acc[U];
 #pragma unroll
       for (int u = 0; u < U; u++) {
         const int64_t q = p + u * GPB;
         acc[u] = q < hi ? gather_dot<HP, true>(r[u], v, pol_v) : 0.0f;
       }
-      const int64_t pn = p + PPB;
 #pragma unroll
       for (int u = 0; u < U; u++) {
         if (LANES >= 4) acc[u] += __shfl_xor_sync(0xffffffffu, acc[u], 2);
         if (LANES >= 2) acc[u] += __shfl_xor_sync(0xffffffffu, acc[u], 1);
         const int64_t q = p + u * GPB;
         if (q < hi && h == 0) st_keep_f(v + q, fmaf(sg[u], x[u], acc[u]), pol_v);
-        const int64_t qn = pn + u * GPB;
-        if (qn < hi) {
-          load_row<HP>(r[u], nb, bw, (qn - n0) * LANES, pol_rows);
-          if (h == 0) {
-            sg[u] = ld_stream_f(sigma + qn, pol_rows);
-            x[u] = ld_stream_f(xi + qn, pol_rows);
-          }
-        }
       }
       p = pn;
     }
@@ -257,13 +287,13 @@ __global__ void __launch_bounds__(256) whiten_tiles_kernel(
         }
         pos = (int64_t)s_start[lo] + (vi - s_pref[lo]);
         Row<HP> r;
-        load_row<HP>(r, nbr + h * HP, b + h * HP, (pos - n0) * LANES, pol_rows);
+        load_row_na<HP>(r, nbr + h * HP, b + h * HP, (pos - n0) * LANES, pol_rows);
         acc = gather_dot<HP, false>(r, v, pol_v);
       }
       if (LANES >= 4) acc += __shfl_xor_sync(0xffffffffu, acc, 2);
       if (LANES >= 2) acc += __shfl_xor_sync(0xffffffffu, acc, 1);
       if (act && h == 0) {
-        float sg = ld_stream_f(sigma + pos, pol_rows);
+        float sg = ld_stream_na_f(sigma + pos, pol_rows);
         float vv = ld_keep_f(v + pos, pol_v);
         float out = (vv - acc) / sg;
         st_stream_f(xi + pos, out, pol_rows);
@@ -295,8 +325,10 @@ int launch_generate(graphgp_graph_t g, graphgp_factor_t f, const float* xi, floa
                     cudaStream_t s) {
   if (g->num_levels <= 1) return GRAPHGP_OK;
   GGP_CUDA(cudaMemsetAsync(g->level_bar, 0, g->num_levels * sizeof(uint32_t), s));
+  constexpr int LANES = gen_lanes(KP), U = gen_steps(KP / LANES);
+  auto kern = generate_kernel<KP, LANES, U>;
   static int max_grid = 0;
-  if (!max_grid) max_grid = coop_grid(generate_kernel<KP, gen_lanes(KP)>, kSweepThreads);
+  if (!max_grid) max_grid = coop_grid(kern, kSweepThreads);
   int64_t want = (g->max_level_size + kSweepThreads - 1) / kSweepThreads;
   int grid = (int)std::min<int64_t>(max_grid, std::max<int64_t>(want, 1));
   LevelBarrier lb{g->level_bar, g->err, g->max_spin};
@@ -308,8 +340,8 @@ int launch_generate(graphgp_graph_t g, graphgp_factor_t f, const float* xi, floa
   int64_t n0 = g->n0;
   void* args[] = {(void*)&nbr, (void*)&bw, (void*)&sg, (void*)&xi, (void*)&v,
                   (void*)&lo,  (void*)&nl, (void*)&n0, (void*)&lb};
-  GGP_CUDA(cudaLaunchCooperativeKernel((const void*)generate_kernel<KP, gen_lanes(KP)>, dim3(grid),
-                                       dim3(kSweepThreads), args, 0, s));
+  GGP_CUDA(cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(kSweepThreads), args, 0,
+                                       s));
   return GRAPHGP_OK;
 }
 
