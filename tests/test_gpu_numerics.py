@@ -81,8 +81,11 @@ def test_tiny_factor_sweeps_logdet(gpu_lib, name):
 
 
 @pytest.mark.parametrize("kind,k", [("gaussian", 16), ("ldr", 16), ("uniform", 32), ("blobs", 5),
-                                    ("uniform", 1)])
+                                    ("uniform", 1), ("uniform", 11), ("gaussian", 19),
+                                    ("blobs", 23), ("uniform", 27)])
 def test_factor_and_sweeps_several_tiles(gpu_lib, kind, k):
+    """Every padded row length of the sweeps (k rounded up to 4, 8, 12, ..., 32)
+    over clouds that span several blocks per level and a ragged last block."""
     N = 20_011
     pts = workloads.cloud(kind, N, 40 + k)
     kern = (1, 1.0, 0.05, 1e-5)
