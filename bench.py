@@ -218,6 +218,49 @@ def serving_bench(n_inst=64, rate=2000.0, duration=5.0, seed=8, n_slots=8):
             "instances_points": total_pts}
 
 
+def differentiation_bench(stream, reps=3):
+    """The differentiation workload (N = 2^22 uniform in [0,1]^3, k = 32,
+    squared exponential l = 0.03, nugget 1e-4, v drawn from the model): the
+    NLL and its gradient with respect to (l, s2, nugget) and v, the factor
+    recomputed in the backward pass."""
+    import torch
+
+    import paper_2606_11402_gb300 as gg
+    import workloads
+    w = workloads.WORKLOADS["diff"]
+    N, k = w["N"], w["k"]
+    pts = torch.from_numpy(workloads.uniform_cube(N, w["seed"])).cuda()
+    kern = gg.Kernel(*w["kernel"])
+    g = gg.build_graph(pts, k)
+    f = gg.factor(g, kern)
+    v = gg.generate(g, f, torch.from_numpy(workloads.white_noise(N, w["xi_seed"])).cuda())
+    out = torch.empty(1, dtype=torch.float64, device="cuda")
+    vbar = torch.empty_like(v)
+    tbar = torch.zeros(3, dtype=torch.float64, device="cuda")
+
+    def step():
+        gg.nll(g, f, v, out=out)
+        gg.nll_backward(g, f, v, vbar=vbar, thetabar=tbar)
+    step()  # builds the children CSR
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        step()
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / reps
+    t0 = time.perf_counter()
+    f2 = gg.factor(g, kern)
+    torch.cuda.synchronize()
+    t_factor = time.perf_counter() - t0
+    st, _ = gg.sync_status(g, f2)
+    return {"workload": "differentiation: N=2^22 uniform [0,1]^3, k=32, squared exponential "
+                        "l=0.03 nugget 1e-4; NLL + gradient (l, s2, nugget, v)",
+            "nll_and_gradient_ms": ms, "points_per_s": N / (ms / 1e3),
+            "factor_ms": t_factor * 1e3, "status": st}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -371,6 +414,28 @@ def run_ours(args):
         fused["generate_points_per_s"] = N / (fused["generate_ms"] / 1e3)
         fused["whiten_points_per_s"] = N / (fused["whiten_ms"] / 1e3)
 
+    # adjoints on the same workload (children CSR built by the untimed first call)
+    def timed_ms(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+    nll_out = torch.empty(1, dtype=torch.float64, device="cuda")
+    vbar = torch.empty_like(v)
+    tbar = torch.zeros(3, dtype=torch.float64, device="cuda")
+    adj = {"nll_ms": timed_ms(lambda: gg.nll(g, f, v, out=nll_out)),
+           "nll_backward_ms": timed_ms(lambda: gg.nll_backward(g, f, v, vbar=vbar, thetabar=tbar)),
+           "generate_backward_ms": timed_ms(
+               lambda: gg.generate_backward(g, f, xi, v, v, xibar=xo, thetabar=tbar))}
+    for key in list(adj):
+        adj[key.replace("_ms", "_points_per_s")] = N / (adj[key] / 1e3)
+    diff = differentiation_bench(stream) if args.diff else None
+
     hbm, peak_kind = _peaks()
     rows = N - g.n0
     bytes_per_point = 8 * k + 16
@@ -400,12 +465,14 @@ def run_ours(args):
                    "whiten_hbm_frac": alg_bytes / (wh_ms / 1e3) / 1e9 / hbm,
                    "graph_build_s": t_graph, "graph_points_per_s": N / t_graph,
                    "factor_s": t_factor, "factor_points_per_s": N / t_factor,
-                   "not_pd_rows": nbad, "fused": fused},
+                   "not_pd_rows": nbad, "fused": fused, "adjoints": adj},
         "e2e": {"value": e2e_value, "unit": UNIT, "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": 4 * N, "d2h_bytes_per_step": 8 * N + 8},
         "gpu_launches": 4 * args.steps,
         "clocks": _clock_summary(os.path.join("/tmp", f"ggp_clocks_{rank}.csv"), local),
     }
+    if diff is not None:
+        line["differentiation"] = diff
     if rank == 0 and not args.no_serve:
         sb = serving_bench(duration=args.serve_duration)
         line["serving"] = sb
@@ -432,6 +499,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving stream")
     ap.add_argument("--serve-duration", type=float, default=5.0)
+    ap.add_argument("--no-diff", dest="diff", action="store_false",
+                    help="skip the differentiation-workload timing")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -25,8 +25,8 @@
  *    before any work is enqueued and leave outputs untouched.  Errors found on
  *    the device (a bounded wait that timed out, a non-positive pivot) are
  *    recorded in the handle and returned by graphgp_sync_status.
- *  - Sizes: 1 <= k <= 32 neighbours, d == 3, k <= n0 <= N, n0 <= 2048,
- *    N < 2^31.
+ *  - Sizes: 1 <= k <= 64 neighbours (the range the paper gives for its GPU
+ *    method, Sec. 2.3), 1 <= d <= 3, k <= n0 <= N, n0 <= 2048, N < 2^31.
  */
 #ifndef GRAPHGP_H
 #define GRAPHGP_H

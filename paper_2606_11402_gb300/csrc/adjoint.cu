@@ -19,7 +19,7 @@
 // theta = (lengthscale, sigma2, nugget); theta_bar is accumulated in FP64.
 #include <algorithm>
 
-#include "pointfactor.cuh"
+#include "pointwide.cuh"
 #include "sweepsync.cuh"
 
 namespace ggp {
@@ -316,6 +316,79 @@ __global__ void __launch_bounds__(128) factor_backward_kernel(
   block_add3(tl, ts, tn, thetabar);
 }
 
+// The same per-row backward for 32 < k <= 64: one warp per point, the factor
+// recomputed by point_factor_wide (bit-identical to the forward kernel), then
+// g = K_cc^-1 bbar by two triangular solves in shared memory.  Lane a + 32 s
+// takes row a + 32 s of Kbar against dK/dtheta (FP32 per row, FP64 across
+// rows); rows needing the FP64 rescue go to factor_backward_rescue_kernel.
+template <int KT>
+__global__ void __launch_bounds__(128) factor_backward_wide_kernel(
+    const float4* __restrict__ xs, const int32_t* __restrict__ nbr, int64_t N, int k, int kp,
+    int64_t n0, KernF kf, int mode, const float* __restrict__ coef, float beta,
+    const float* __restrict__ v, const float* __restrict__ xi, float* __restrict__ xibar_out,
+    double* __restrict__ thetabar, int64_t* __restrict__ rescue_rows,
+    unsigned long long* __restrict__ rescue_count) {
+  extern __shared__ __align__(16) unsigned char wide_smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  WideWarp& W = reinterpret_cast<WideWarp*>(wide_smem)[warp];
+  double tl = 0.0, ts = 0.0, tn = 0.0;
+  const float inv_s2 = 1.0f / kf.s2;
+  const int64_t npts = N - n0;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t t = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; t < npts; t += nw) {
+    const int64_t i = n0 + t;
+    const int32_t* row = nbr + t * kp;
+    for (int a = lane; a < k; a += 32) W.x[a] = __ldg(xs + row[a]);
+    __syncwarp();
+    const float4 xq = __ldg(xs + i);
+    const WideFactor r = point_factor_wide<KT>(W, k, kf, xq);
+    if (wide_needs_rescue(W, r, k, kf)) {
+      if (lane == 0) rescue_rows[atomicAdd(rescue_count, 1ull)] = i;
+      __syncwarp();
+      continue;
+    }
+    const float sigma = r.sigma;
+    const float ci = coef[i];
+    const float alpha = mode == 0 ? -ci / sigma : ci;
+    const float sigbar = alpha * xi[i] + beta / sigma;
+    const float sbar = sigbar / (2.0f * sigma);
+    for (int a = lane; a < k; a += 32) W.g[a] = alpha * v[row[a]];
+    __syncwarp();
+    wide_chol_solve(W, k);
+    for (int a = lane; a < k; a += 32) {
+      const float ga = W.g[a], ba = W.y[a];
+      const float4 xa = W.x[a];
+      float pl = 0.0f, ps = 0.0f, pn = 0.0f;
+      for (int c = 0; c < k; c++) {
+        const float bc = W.y[c];
+        const float kb = -ga * bc + sbar * ba * bc;
+        if (c == a) {
+          ps += kb;
+          pn += kb;
+        } else {
+          const float d2 = sqdist(xa, W.x[c]);
+          ps += kb * kappa_d2<KT>(kf, d2) * inv_s2;
+          pl += kb * dkappa_dell_d2<KT>(kf, d2);
+        }
+      }
+      const float kci = ga - 2.0f * sbar * ba;
+      const float d2q = sqdist(xa, xq);
+      ps += kci * kappa_d2<KT>(kf, d2q) * inv_s2;
+      pl += kci * dkappa_dell_d2<KT>(kf, d2q);
+      tl += pl;
+      ts += ps;
+      tn += pn;
+    }
+    if (lane == 0) {  // Kbar_ii = sbar
+      ts += sbar;
+      tn += sbar;
+      if (mode == 1) xibar_out[i] = sigma * ci;
+    }
+    __syncwarp();
+  }
+  block_add3(tl, ts, tn, thetabar);
+}
+
 // FP64 backward of the rows the lane-group kernel handed over (rescue.cuh).
 template <int G, int KT>
 __global__ void __launch_bounds__(128) factor_backward_rescue_kernel(
@@ -500,6 +573,41 @@ int launch_factor_backward_thread(graphgp_graph_t g, graphgp_factor_t f, int mod
   return GRAPHGP_OK;
 }
 
+int launch_factor_backward_wide(graphgp_graph_t g, graphgp_factor_t f, int mode,
+                                const float* coef, float beta, const float* v, const float* xi,
+                                float* xibar, double* thetabar, cudaStream_t s) {
+  const int64_t npts = g->N - g->n0;
+  if (npts <= 0) return GRAPHGP_OK;
+  constexpr int kWarps = 4;
+  const size_t smem = kWarps * sizeof(WideWarp);
+  const unsigned grid = grid_for((npts + kWarps - 1) / kWarps * 128, 128, 4);
+  KernF kf = make_kernf(f->kern);
+  Scratch sc(s);
+  int64_t* rows = nullptr;
+  unsigned long long* cnt = nullptr;
+  GGP_TRY(sc.alloc(&rows, npts));
+  GGP_TRY(sc.alloc(&cnt, 1));
+  GGP_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), s));
+  const unsigned rgrid = (unsigned)num_sms() * 2;
+#define GGP_FBW(KT)                                                                            \
+  GGP_CUDA(cudaFuncSetAttribute(factor_backward_wide_kernel<KT>,                               \
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));      \
+  factor_backward_wide_kernel<KT><<<grid, 32 * kWarps, smem, s>>>(                             \
+      g->xs, g->nbr, g->N, g->k, g->kp, g->n0, kf, mode, coef, beta, v, xi, xibar, thetabar,   \
+      rows, cnt);                                                                              \
+  factor_backward_rescue_kernel<kWideK, KT><<<rgrid, 128, 0, s>>>(                             \
+      g->xs, g->nbr, g->k, g->kp, g->n0, kf, mode, coef, beta, v, xi, xibar, thetabar, rows, cnt)
+  switch (f->kern.type) {
+    case GRAPHGP_MATERN12: GGP_FBW(GRAPHGP_MATERN12); break;
+    case GRAPHGP_MATERN32: GGP_FBW(GRAPHGP_MATERN32); break;
+    case GRAPHGP_MATERN52: GGP_FBW(GRAPHGP_MATERN52); break;
+    default: GGP_FBW(GRAPHGP_SQEXP); break;
+  }
+#undef GGP_FBW
+  GGP_CUDA(cudaGetLastError());
+  return GRAPHGP_OK;
+}
+
 int factor_backward(graphgp_graph_t g, graphgp_factor_t f, int mode, const float* coef,
                     float beta, const float* v, const float* xi, float* xibar, double* thetabar,
                     cudaStream_t s) {
@@ -508,7 +616,11 @@ int factor_backward(graphgp_graph_t g, graphgp_factor_t f, int mode, const float
     case 8: return launch_factor_backward_thread<8>(g, f, mode, coef, beta, v, xi, xibar, thetabar, s);
     case 12: return launch_factor_backward_thread<12>(g, f, mode, coef, beta, v, xi, xibar, thetabar, s);
     case 16: return launch_factor_backward_thread<16>(g, f, mode, coef, beta, v, xi, xibar, thetabar, s);
-    default: return launch_factor_backward<32>(g, f, mode, coef, beta, v, xi, xibar, thetabar, s);
+    case 20:
+    case 24:
+    case 28:
+    case 32: return launch_factor_backward<32>(g, f, mode, coef, beta, v, xi, xibar, thetabar, s);
+    default: return launch_factor_backward_wide(g, f, mode, coef, beta, v, xi, xibar, thetabar, s);
   }
 }
 

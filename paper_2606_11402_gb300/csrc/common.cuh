@@ -98,9 +98,13 @@ struct Scratch {
 };
 
 // Rows of the neighbour and weight matrices are padded to a multiple of four
-// entries so that every row starts on a 16-byte boundary; padding entries
-// point at position 0 with weight 0.
-inline int row_stride(int k) { return (k + 3) & ~3; }
+// entries (sixteen for k > 32, which keeps the number of compiled sweep
+// variants small) so that every row starts on a 16-byte boundary; padding
+// entries point at position 0 with weight 0.
+inline int row_stride(int k) { return k <= 32 ? (k + 3) & ~3 : (k + 15) & ~15; }
+
+// Largest number of neighbours per point.
+constexpr int kMaxK = 64;
 
 // Spatial tile of the whiten sweep: this many consecutive k-d in-order ranks.
 constexpr int64_t kTileR = 4096;

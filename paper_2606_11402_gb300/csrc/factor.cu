@@ -14,7 +14,7 @@
 // raised to that floor and counted.  logdet = sum log sigma_i^2 is reduced in
 // FP64 from the stored FP32 sigma (a running FP64 product with separate
 // exponent, one log per thread).
-#include "pointfactor.cuh"
+#include "pointwide.cuh"
 
 namespace ggp {
 namespace {
@@ -118,6 +118,53 @@ __global__ void __launch_bounds__(128) point_factor_thread_kernel(
   block_add_double(acc.log_value(), logdet);
   for (int o = 16; o; o >>= 1) clamped_rows += __shfl_xor_sync(0xffffffffu, clamped_rows, o);
   if ((threadIdx.x & 31) == 0 && clamped_rows) atomicAdd(not_pd, clamped_rows);
+}
+
+// 32 < k <= 64: one warp per point with the factor in shared memory
+// (pointwide.cuh).  Rows that need the FP64 rescue are recomputed by lane 0.
+template <int KT>
+__global__ void __launch_bounds__(128) point_factor_wide_kernel(
+    const float4* __restrict__ xs, const int32_t* __restrict__ nbr, int64_t N, int k, int kp,
+    int64_t n0, KernF kf, float* __restrict__ b_out, float* __restrict__ sigma_out,
+    double* __restrict__ logdet, unsigned long long* __restrict__ not_pd) {
+  extern __shared__ __align__(16) unsigned char wide_smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  WideWarp& W = reinterpret_cast<WideWarp*>(wide_smem)[warp];
+  LogAcc acc;
+  unsigned long long clamped_rows = 0;
+  const int64_t npts = N - n0;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t t = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; t < npts; t += nw) {
+    const int64_t i = n0 + t;
+    const int32_t* row = nbr + t * kp;
+    for (int a = lane; a < k; a += 32) W.x[a] = __ldg(xs + row[a]);
+    __syncwarp();
+    const float4 xq = __ldg(xs + i);
+    WideFactor r = point_factor_wide<KT>(W, k, kf, xq);
+    if (wide_needs_rescue(W, r, k, kf)) {
+      if (lane == 0) {
+        Row64<kWideK> R;
+        row_factor64<kWideK, KT>(R, xs, row, k, xq, kf);
+        for (int e = 0; e < kp; e++) b_out[t * kp + e] = e < k ? (float)R.b[e] : 0.0f;
+        const float sg = (float)R.sigma;
+        sigma_out[i] = sg;
+        acc.mul(sg);
+        if (R.clamped) clamped_rows++;
+      }
+    } else {
+      for (int a = lane; a < kp; a += 32) b_out[t * kp + a] = a < k ? W.y[a] : 0.0f;
+      if (lane == 0) {
+        sigma_out[i] = r.sigma;
+        acc.mul(r.sigma);
+        if (r.clamped) clamped_rows++;
+      }
+    }
+    __syncwarp();
+  }
+  double lv = (lane == 0) ? acc.log_value() : 0.0;
+  block_add_double(lv, logdet);
+  for (int o = 16; o; o >>= 1) clamped_rows += __shfl_xor_sync(0xffffffffu, clamped_rows, o);
+  if (lane == 0 && clamped_rows) atomicAdd(not_pd, clamped_rows);
 }
 
 // Dense block: K_00 (lower triangle) in global memory.
@@ -332,6 +379,29 @@ int launch_point_thread(int type, graphgp_graph_t g, graphgp_factor_t f, const K
   return GRAPHGP_OK;
 }
 
+constexpr int kWideWarps = 4;  // warps per block of the wide kernels
+
+int launch_point_wide(int type, graphgp_graph_t g, graphgp_factor_t f, const KernF& kf,
+                      cudaStream_t s) {
+  const int64_t npts = g->N - g->n0;
+  const size_t smem = kWideWarps * sizeof(WideWarp);
+  const unsigned grid = grid_for((npts + kWideWarps - 1) / kWideWarps * 128, 128, 4);
+#define GGP_PW(KT)                                                                           \
+  GGP_CUDA(cudaFuncSetAttribute(point_factor_wide_kernel<KT>,                                \
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));    \
+  point_factor_wide_kernel<KT><<<grid, 32 * kWideWarps, smem, s>>>(                          \
+      g->xs, g->nbr, g->N, g->k, g->kp, g->n0, kf, f->b, f->sigma, f->logdet, f->not_pd)
+  switch (type) {
+    case GRAPHGP_MATERN12: GGP_PW(GRAPHGP_MATERN12); break;
+    case GRAPHGP_MATERN32: GGP_PW(GRAPHGP_MATERN32); break;
+    case GRAPHGP_MATERN52: GGP_PW(GRAPHGP_MATERN52); break;
+    default: GGP_PW(GRAPHGP_SQEXP); break;
+  }
+#undef GGP_PW
+  GGP_CUDA(cudaGetLastError());
+  return GRAPHGP_OK;
+}
+
 }  // namespace
 
 int point_factor(graphgp_graph_t g, graphgp_factor_t f, const KernF& kf, int type,
@@ -342,7 +412,11 @@ int point_factor(graphgp_graph_t g, graphgp_factor_t f, const KernF& kf, int typ
     case 8: return launch_point_thread<8>(type, g, f, kf, s);
     case 12: return launch_point_thread<12>(type, g, f, kf, s);
     case 16: return launch_point_thread<16>(type, g, f, kf, s);
-    default: return launch_point<32>(type, g, f, kf, s);
+    case 20:
+    case 24:
+    case 28:
+    case 32: return launch_point<32>(type, g, f, kf, s);
+    default: return launch_point_wide(type, g, f, kf, s);
   }
 }
 

@@ -248,7 +248,7 @@ extern "C" int graphgp_build_graph(const float* points_d, int64_t N, int d, int 
                                    graphgp_graph_t* out) {
   if (!out) return GRAPHGP_ERR_INVALID;
   *out = nullptr;
-  if (!points_d || N < 1 || N >= ((int64_t)1 << 31) || d < 1 || d > 3 || k < 1 || k > 32)
+  if (!points_d || N < 1 || N >= ((int64_t)1 << 31) || d < 1 || d > 3 || k < 1 || k > kMaxK)
     return GRAPHGP_ERR_INVALID;
   int n0 = opts && opts->n0 > 0 ? opts->n0 : (int)std::min<int64_t>(N, std::max(k, 256));
   int rule = opts ? opts->split_rule : 0;
@@ -384,7 +384,7 @@ extern "C" int graphgp_graph_import(const float* points_h, int64_t N, int k, int
   if (!out) return GRAPHGP_ERR_INVALID;
   *out = nullptr;
   if (!points_h || !order_h || !level_offsets_h || N < 1 || N >= ((int64_t)1 << 31) || k < 1 ||
-      k > 32 || n0 < k || n0 > N || n0 > 2048 || num_levels < 1 || (N > n0 && !nbr_h))
+      k > kMaxK || n0 < k || n0 > N || n0 > 2048 || num_levels < 1 || (N > n0 && !nbr_h))
     return GRAPHGP_ERR_INVALID;
   // validation on the host: order is a permutation, levels are consistent,
   // every neighbour lies in an earlier level
@@ -537,7 +537,7 @@ extern "C" int graphgp_graph_load(const char* path, void* stream, graphgp_graph_
   int32_t hdr[4];
   bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kMagic, 8) == 0 &&
             std::fread(&N, 8, 1, f) == 1 && std::fread(hdr, 4, 4, f) == 4 && hdr[0] == 1 &&
-            N >= 1 && N < ((int64_t)1 << 31) && hdr[1] >= 1 && hdr[1] <= 32 && hdr[2] >= 1 &&
+            N >= 1 && N < ((int64_t)1 << 31) && hdr[1] >= 1 && hdr[1] <= kMaxK && hdr[2] >= 1 &&
             hdr[2] <= N && hdr[3] >= 1 && hdr[3] <= N;
   if (!ok) {
     std::fclose(f);

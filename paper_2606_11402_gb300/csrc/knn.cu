@@ -149,8 +149,10 @@ int knn_query(const float* pts, const int32_t* tree_point,
     knn_kernel<8><<<grid, B, 0, s>>>(xt, node_at_inorder, N, k, n0, nbr_tree, err);
   else if (k <= 16)
     knn_kernel<16><<<grid, B, 0, s>>>(xt, node_at_inorder, N, k, n0, nbr_tree, err);
-  else
+  else if (k <= 32)
     knn_kernel<32><<<grid, B, 0, s>>>(xt, node_at_inorder, N, k, n0, nbr_tree, err);
+  else
+    knn_kernel<64><<<grid, B, 0, s>>>(xt, node_at_inorder, N, k, n0, nbr_tree, err);
   GGP_CUDA(cudaGetLastError());
   return GRAPHGP_OK;
 }

@@ -238,7 +238,9 @@ extern "C" int graphgp_nll_noalloc(graphgp_graph_t g, graphgp_factor_t f, const 
       case 20: rc = launch_tiles<20>(g, f, v_d, slot, s); break;
       case 24: rc = launch_tiles<24>(g, f, v_d, slot, s); break;
       case 28: rc = launch_tiles<28>(g, f, v_d, slot, s); break;
-      default: rc = launch_tiles<32>(g, f, v_d, slot, s); break;
+      case 32: rc = launch_tiles<32>(g, f, v_d, slot, s); break;
+      case 48: rc = launch_tiles<48>(g, f, v_d, slot, s); break;
+      default: rc = launch_tiles<64>(g, f, v_d, slot, s); break;
     }
     if (rc < 0) return rc;
   }

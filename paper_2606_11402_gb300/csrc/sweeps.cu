@@ -374,7 +374,9 @@ int launch_whiten(graphgp_graph_t g, graphgp_factor_t f, const float* v, float* 
     case 20: call(20); break;                \
     case 24: call(24); break;                \
     case 28: call(28); break;                \
-    default: call(32); break;                \
+    case 32: call(32); break;                \
+    case 48: call(48); break;                \
+    default: call(64); break;                \
   }
 
 }  // namespace

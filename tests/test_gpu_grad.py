@@ -20,6 +20,9 @@ CASES = [
     ("uniform", 4096, 16, (3, 1.0, 0.03, 1e-4)),
     ("gaussian", 3000, 16, (1, 1.0, 0.1, 1e-6)),
     ("ldr", 3000, 5, (2, 1.2, 0.1, 1e-3)),
+    # 32 < k <= 64: one warp per point, the factor in shared memory
+    ("uniform", 3000, 48, (1, 1.0, 0.03, 1e-4)),
+    ("gaussian", 3000, 64, (0, 1.0, 0.1, 1e-4)),
 ]
 
 

@@ -56,7 +56,7 @@ def test_tiny_workload_graph_is_bit_exact(gpu_lib):
 
 @pytest.mark.parametrize("kind", ["uniform", "gaussian", "ldr", "blobs", "grid", "dups", "flat",
                                   "negzero"])
-@pytest.mark.parametrize("k", [1, 5, 16, 32])
+@pytest.mark.parametrize("k", [1, 5, 16, 32, 33, 64])
 def test_graph_bit_exact_clouds(gpu_lib, kind, k):
     # 5003 points: several radix-sort tiles (2048) and sweep chunks plus a tail
     pts = _cloud(kind, 5003, 100 + k)
@@ -70,7 +70,8 @@ def test_graph_split_rules(gpu_lib, rule):
 
 
 @pytest.mark.parametrize("N,k,n0", [(1, 1, 1), (2, 1, 1), (3, 2, 2), (64, 8, 64), (65, 8, 64),
-                                    (257, 16, 256), (1000, 32, 32), (2049, 4, 2048)])
+                                    (257, 16, 256), (1000, 32, 32), (2049, 4, 2048),
+                                    (64, 64, 64), (65, 64, 64), (700, 48, 48)])
 def test_graph_edge_sizes(gpu_lib, N, k, n0):
     pts = workloads.unit_gaussian(N, N)
     _compare(gpu_lib, pts, k, n0=n0)
@@ -109,7 +110,7 @@ def test_graph_rejects_bad_input(gpu_lib):
         gpu_lib.build_graph(to_gpu(pts), 8)
     assert e.value.status == gpu_lib.ERR_NAN
     with pytest.raises(gpu_lib.GraphGPError):
-        gpu_lib.build_graph(to_gpu(workloads.uniform_cube(100, 1)), 33)
+        gpu_lib.build_graph(to_gpu(workloads.uniform_cube(100, 1)), 65)
     with pytest.raises(gpu_lib.GraphGPError):
         gpu_lib.build_graph(to_gpu(workloads.uniform_cube(100, 1)), 8, n0=4)
 

@@ -82,13 +82,18 @@ def test_tiny_factor_sweeps_logdet(gpu_lib, name):
 
 @pytest.mark.parametrize("kind,k", [("gaussian", 16), ("ldr", 16), ("uniform", 32), ("blobs", 5),
                                     ("uniform", 1), ("uniform", 11), ("gaussian", 19),
-                                    ("blobs", 23), ("uniform", 27)])
+                                    ("blobs", 23), ("uniform", 27), ("gaussian", 33),
+                                    ("uniform", 48), ("uniform", 64)])
 def test_factor_and_sweeps_several_tiles(gpu_lib, kind, k):
-    """Every padded row length of the sweeps (k rounded up to 4, 8, 12, ..., 32)
-    over clouds that span several blocks per level and a ragged last block."""
+    """Every padded row length of the sweeps (k rounded up to 4, 8, 12, ..., 32,
+    then 48, 64) and every factor path (one thread, a 32-lane group, one warp
+    with the matrix in shared memory) over clouds that span several blocks per
+    level and a ragged last block."""
     N = 20_011
     pts = workloads.cloud(kind, N, 40 + k)
-    kern = (1, 1.0, 0.05, 1e-5)
+    # beyond 32 neighbours the Matern-3/2 conditionals of these clouds lose
+    # most FP32 digits (cond(K_cc) grows with k); Matern-1/2 keeps the check tight
+    kern = (1, 1.0, 0.05, 1e-5) if k <= 32 else (0, 1.0, 0.05, 1e-5)
     g, f, want, fo = _setup(gpu_lib, pts, k, kern, n0=max(k, 128))
     tol = fp32_tolerance(want, kern)
     _check_factor(gpu_lib, g, f, want, fo, tol)

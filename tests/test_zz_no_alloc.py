@@ -22,7 +22,7 @@ pytestmark = pytest.mark.gpu
 
 
 @pytest.mark.parametrize("N,k,kind", [(20_011, 16, "gaussian"), (3000, 8, "uniform"),
-                                      (300, 8, "uniform")])
+                                      (300, 8, "uniform"), (5000, 48, "uniform")])
 def test_nll_noalloc_matches_nll_on_two_calls(gpu_lib, N, k, kind):
     pts = torch.from_numpy(workloads.cloud(kind, N, 77)).cuda()
     g = gpu_lib.build_graph(pts, k, n0=min(N, 256))
