@@ -96,6 +96,9 @@ def _declare(L):
         "oracle_whiten_vjp": (None, [_P, _P, _P, _P, _I64, _I, _I64, _P, _P, _P, _D, _P, _P, _P, _P]),
         "oracle_generate_vjp": (None, [_P, _P, _P, _P, _I64, _I, _I64, _P, _P, _P, _P, _P, _P, _P]),
         "oracle_factor_backward": (_I, [_P, _P, _I64, _I, _I64, _I, _D, _D, _D, _P, _P, _P, _P]),
+        "oracle_kappa_h": (_D, [_I, _D, _D, _D]),
+        "oracle_factor_backward_points": (_I, [_P, _P, _I64, _I, _I64, _I, _D, _D, _D, _P, _P, _P,
+                                                _P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -370,3 +373,29 @@ def nll_grad(g, kern: Kernel, v):
     a = whiten_vjp(fac, g["nbr_pos"], k, n0, v, xi, xi, 0.5)
     tb = factor_backward(g["pts_pos"], g["nbr_pos"], k, n0, kern, a["bbar"], a["bdbar"], a["sigbar"])
     return a["vbar"], tb
+
+
+def kappa_h(kern: Kernel, r):
+    """kappa'(r) / r (0 at r = 0 for Matern-1/2)."""
+    return lib().oracle_kappa_h(kern.type, kern.sigma2, kern.lengthscale, float(r))
+
+
+def nll_grad_points(g, kern: Kernel, v):
+    """Gradient of nll(v; points) with respect to the point coordinates, the
+    graph (order, neighbour lists, levels) held fixed.  Returns float64[N, 3]
+    in INPUT order (the layout of the points given to build_graph)."""
+    k, n0 = g["k"], g["n0"]
+    fac = factor(g["pts_pos"], g["nbr_pos"], k, n0, kern)
+    xi = whiten(fac, g["nbr_pos"], k, n0, v)
+    a = whiten_vjp(fac, g["nbr_pos"], k, n0, v, xi, xi, 0.5)
+    pp = _c(g["pts_pos"], np.float32)
+    N = pp.shape[0]
+    xb = np.zeros((N, 3), np.float64)
+    _check(lib().oracle_factor_backward_points(
+        _p(pp), _p(_c(g["nbr_pos"], np.int32)), N, k, n0, kern.type, kern.sigma2,
+        kern.lengthscale, kern.nugget, _p(_c(a["bbar"], np.float64)),
+        _p(_c(a["bdbar"], np.float64)), _p(_c(a["sigbar"], np.float64)), _p(xb)),
+        "factor_backward_points")
+    out = np.empty_like(xb)
+    out[np.asarray(g["order"], np.int64)] = xb
+    return out

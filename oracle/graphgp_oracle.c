@@ -771,3 +771,108 @@ int oracle_factor_backward(const float* pts_pos, const int32_t* nbr_pos,
   free(idx);
   return ORC_OK;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Derivative of the covariance with respect to the distance, divided by the
+ * distance: h(r) = kappa'(r) / r, so that d kappa(|x_a - x_b|) / d x_a =
+ * h(r) (x_a - x_b).  Matern-1/2 is not differentiable at r = 0; there the
+ * direction x_a - x_b vanishes and h is taken as 0.                        */
+/* ------------------------------------------------------------------------ */
+double oracle_kappa_h(int type, double s2, double ell, double r) {
+  switch (type) {
+    case 0: return r > 0.0 ? -s2 * exp(-r / ell) / (ell * r) : 0.0;
+    case 1: { double a = sqrt(3.0) * r / ell; return -3.0 * s2 * exp(-a) / (ell * ell); }
+    case 2: {
+      double a = sqrt(5.0) * r / ell;
+      return -5.0 * s2 * (1.0 + a) * exp(-a) / (3.0 * ell * ell);
+    }
+    case 3: return -s2 * exp(-r * r / (2.0 * ell * ell)) / (ell * ell);
+  }
+  return NAN;
+}
+
+/* Gradient with respect to the point coordinates (graph order), with the
+ * graph held fixed, from the same per-row cotangents as
+ * oracle_factor_backward: every covariance entry K_ab = kappa(|x_a - x_b|)
+ * of row i (neighbour-neighbour and neighbour-point) passes its cotangent
+ * Kbar_ab on to both of its points:  xbar_a += Kbar_ab h(r) (x_a - x_b),
+ * xbar_b -= Kbar_ab h(r) (x_a - x_b).  xbar is [N][3], accumulated (+=).   */
+int oracle_factor_backward_points(const float* pts_pos, const int32_t* nbr_pos,
+                                  int64_t N, int k, int64_t n0, int type, double s2,
+                                  double ell, double nug, const double* bbar,
+                                  const double* bdbar, const double* sigbar,
+                                  double* xbar) {
+  double k0 = oracle_kappa(type, s2, ell, 0.0) + nug;
+  int64_t kmax = (k > n0) ? k : n0;
+  double* L = (double*)malloc((size_t)(kmax > 0 ? kmax * kmax : 1) * sizeof(double));
+  double* L0 = (double*)malloc((size_t)(n0 > 0 ? n0 * n0 : 1) * sizeof(double));
+  double* bb = (double*)malloc((size_t)(kmax > 0 ? kmax : 1) * sizeof(double));
+  double* g = (double*)malloc((size_t)(kmax > 0 ? kmax : 1) * sizeof(double));
+  int64_t* idx = (int64_t*)malloc((size_t)(kmax + 1) * sizeof(int64_t));
+  if (!L || !L0 || !bb || !g || !idx) { free(L); free(L0); free(bb); free(g); free(idx); return ORC_ERR; }
+  for (int64_t i = 0; i < n0; i++)
+    for (int64_t j = 0; j < n0; j++)
+      L0[i * n0 + j] = (i == j) ? k0 : oracle_kappa(type, s2, ell, dist64(pts_pos + 3 * i, pts_pos + 3 * j));
+  chol_rows(L0, n0, n0);
+  for (int64_t i = 0; i < N; i++) {
+    int64_t kc;
+    const double* Lc;
+    int64_t ldl;
+    if (i < n0) {
+      kc = i;
+      for (int64_t m = 0; m < kc; m++) idx[m] = m;
+      Lc = L0;
+      ldl = n0;
+      for (int64_t m = 0; m < kc; m++) g[m] = bdbar[i * n0 + m];
+    } else {
+      const int32_t* row = nbr_pos + (i - n0) * k;
+      kc = row_count(row, k);
+      for (int64_t a = 0; a < kc; a++) idx[a] = row[a];
+      for (int64_t a = 0; a < kc; a++)
+        for (int64_t c = 0; c < kc; c++)
+          L[a * kc + c] = (a == c) ? k0 : oracle_kappa(type, s2, ell, dist64(pts_pos + 3 * idx[a], pts_pos + 3 * idx[c]));
+      chol_rows(L, kc, kc);
+      Lc = L;
+      ldl = kc;
+      for (int64_t a = 0; a < kc; a++) g[a] = bbar[(i - n0) * k + a];
+    }
+    for (int64_t a = 0; a < kc; a++)
+      bb[a] = oracle_kappa(type, s2, ell, dist64(pts_pos + 3 * idx[a], pts_pos + 3 * i));
+    solve_lower(Lc, kc, ldl, bb);
+    double s = k0;
+    for (int64_t a = 0; a < kc; a++) s -= bb[a] * bb[a];
+    double sigma = sqrt(s);
+    solve_upper_t(Lc, kc, ldl, bb);
+    double sbar = sigbar[i] / (2.0 * sigma);
+    solve_lower(Lc, kc, ldl, g);
+    solve_upper_t(Lc, kc, ldl, g); /* g = K_cc^-1 bbar */
+    const float* xi = pts_pos + 3 * i;
+    for (int64_t a = 0; a < kc; a++) {
+      const float* xa = pts_pos + 3 * idx[a];
+      /* K_ci[a] = kappa(|x_a - x_i|), cotangent g_a - 2 sbar b_a */
+      double w = (g[a] - 2.0 * sbar * bb[a]) * oracle_kappa_h(type, s2, ell, dist64(xa, xi));
+      for (int d = 0; d < 3; d++) {
+        double dd = (double)xa[d] - (double)xi[d];
+        xbar[3 * idx[a] + d] += w * dd;
+        xbar[3 * i + d] -= w * dd;
+      }
+      for (int64_t c = 0; c < kc; c++) {
+        if (c == a) continue; /* kappa(0) + nugget does not move */
+        const float* xc = pts_pos + 3 * idx[c];
+        double kbar = -g[a] * bb[c] + sbar * bb[a] * bb[c];
+        double wc = kbar * oracle_kappa_h(type, s2, ell, dist64(xa, xc));
+        for (int d = 0; d < 3; d++) {
+          double dd = (double)xa[d] - (double)xc[d];
+          xbar[3 * idx[a] + d] += wc * dd;
+          xbar[3 * idx[c] + d] -= wc * dd;
+        }
+      }
+    }
+  }
+  free(L);
+  free(L0);
+  free(bb);
+  free(g);
+  free(idx);
+  return ORC_OK;
+}

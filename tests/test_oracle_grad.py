@@ -112,3 +112,55 @@ def test_variance_gradient_closed_form():
     xi1 = oracle.whiten(fac1, g["nbr_pos"], k, n0, v)
     _, tb = oracle.nll_grad(g, kern, v)
     assert tb[1] == pytest.approx((N - xi1 @ xi1 / s2) / (2 * s2), rel=1e-9)
+
+
+# ---- gradient with respect to the point coordinates (graph held fixed) ------
+
+def _nll_at(g, kern, v, pts_pos):
+    fac = oracle.factor(pts_pos, g["nbr_pos"], g["k"], g["n0"], kern)
+    return oracle.nll(fac, g["nbr_pos"], g["k"], g["n0"], v)
+
+
+@pytest.mark.parametrize("name", sorted(KERNS))
+def test_point_gradient_by_finite_differences(name):
+    """Central differences on single coordinates.  The step 2^-12 is exact in
+    FP32 for coordinates in [0, 1), so the perturbed points are exactly the
+    intended ones; the graph (order and neighbour lists) stays as built."""
+    kern = KERNS[name]
+    g = _graph(N=300, k=6, n0=20, seed=47)
+    fac = oracle.factor(g["pts_pos"], g["nbr_pos"], g["k"], g["n0"], kern)
+    v = oracle.generate(fac, g["nbr_pos"], g["k"], g["n0"],
+                        workloads.white_noise(g["N"], 48).astype(np.float64))
+    xb = oracle.nll_grad_points(g, kern, v)  # input order
+    order = np.asarray(g["order"])
+    rng = np.random.default_rng(5)
+    h = 2.0 ** -12
+    # positions from the dense block, the first sparse rows and the last ones
+    for pos in (3, 17, 21, 150, g["N"] - 1):
+        for d in rng.choice(3, size=2, replace=False):
+            pp, pm = g["pts_pos"].copy(), g["pts_pos"].copy()
+            pp[pos, d] += np.float32(h)
+            pm[pos, d] -= np.float32(h)
+            fd = (_nll_at(g, kern, v, pp) - _nll_at(g, kern, v, pm)) / (2 * h)
+            got = xb[order[pos], d]
+            assert got == pytest.approx(fd, rel=2e-3, abs=1e-5 * np.abs(xb).max()), (pos, d)
+
+
+@pytest.mark.parametrize("name", ["matern32", "sqexp", "matern52"])
+def test_point_gradient_invariances(name):
+    """A stationary kernel makes the NLL invariant under a common shift of the
+    points (sum of the point gradients = 0), and homogeneous of degree 0 in
+    (points, lengthscale) jointly, so sum_p x_p . xbar_p = -l dNLL/dl with the
+    lengthscale derivative of the (separately pinned) parameter gradient."""
+    kern = KERNS[name]
+    g = _graph(N=400, k=8, n0=24, seed=49)
+    fac = oracle.factor(g["pts_pos"], g["nbr_pos"], g["k"], g["n0"], kern)
+    v = oracle.generate(fac, g["nbr_pos"], g["k"], g["n0"],
+                        workloads.white_noise(g["N"], 50).astype(np.float64))
+    xb = oracle.nll_grad_points(g, kern, v)
+    scale = np.abs(xb).sum()
+    assert np.all(np.abs(xb.sum(axis=0)) <= 1e-10 * scale)
+    _, tb = oracle.nll_grad(g, kern, v)
+    pts = np.asarray(g["pts"], np.float64)  # input order, like xb
+    euler = float((pts * xb).sum())
+    assert euler == pytest.approx(-kern.lengthscale * tb[0], rel=1e-8)
