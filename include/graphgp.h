@@ -239,6 +239,20 @@ int graphgp_nll_backward(graphgp_graph_t g, graphgp_factor_t f,
                          const float* v_d, double nllbar, float* vbar_d,
                          double* thetabar_d, void* stream);
 
+/* Gradient of nll(v) times nllbar with respect to the point coordinates
+ * (Sec. 2.3's derivatives carried through the stationary kernel kappa(r) to
+ * the points), with the graph -- order, neighbour lists, depth levels --
+ * held fixed, as it is for every other derivative here.  pbar_d is
+ * float[N][3] in INPUT order (the layout of the points given to
+ * graphgp_build_graph; for d < 3 the trailing columns belong to the zero
+ * padding), overwritten.  Matern-1/2 is not differentiable at r = 0; a pair
+ * of coincident points contributes 0 there.  Uses the graph's work vectors
+ * (do not overlap with other calls on the graph) and allocates
+ * stream-ordered scratch of 24 N bytes. */
+int graphgp_nll_backward_points(graphgp_graph_t g, graphgp_factor_t f,
+                                const float* v_d, double nllbar, float* pbar_d,
+                                void* stream);
+
 /* ---- serving (continuous batching over resident instances) -------------
  * Not a paper algorithm: an engine that serves the operations above, each
  * request on one resident instance (a graph with its factor).  A native

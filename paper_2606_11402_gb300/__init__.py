@@ -92,6 +92,7 @@ def load() -> ctypes.CDLL:
             "graphgp_generate_backward": [_P, _P, _P, _P, _P, _P, _P, _P],
             "graphgp_whiten_backward": [_P, _P, _P, _P, _P, ctypes.c_double, _P, _P, _P],
             "graphgp_nll_backward": [_P, _P, _P, ctypes.c_double, _P, _P, _P],
+            "graphgp_nll_backward_points": [_P, _P, _P, ctypes.c_double, _P, _P],
             "graphgp_selftest_wait_timeout": [_I64, _P],
             "graphgp_generate_fused": [_P, _P, _P, _P, _P, _P],
             "graphgp_whiten_fused": [_P, _P, _P, _P, _P, _P, _P],
@@ -406,3 +407,15 @@ def nll_backward(graph, fac, v, nllbar=1.0, vbar=None, thetabar=None, stream=Non
                                        _dev(tb, torch.float64, 3, "thetabar"), _stream(stream)),
            "nll_backward")
     return vb, tb
+
+
+def nll_backward_points(graph, fac, v, nllbar=1.0, out=None, stream=None):
+    """nllbar * dNLL/d(points) with the graph held fixed: float32[N, 3] in
+    input order (the layout of the points given to build_graph)."""
+    pb = torch.empty((graph.N, 3), dtype=torch.float32, device="cuda") if out is None else out
+    _check(load().graphgp_nll_backward_points(graph.handle, fac.handle,
+                                              _dev(v, torch.float32, graph.N, "v"), float(nllbar),
+                                              _dev(pb, torch.float32, 3 * graph.N, "pbar"),
+                                              _stream(stream)),
+           "nll_backward_points")
+    return pb

@@ -625,20 +625,38 @@ int factor_backward(graphgp_graph_t g, graphgp_factor_t f, int mode, const float
 }
 
 // Dense block backward from Lbar0 (built from u, xi_0 by dense_lbar_kernel).
+}  // namespace
+
+// Kbar_00 (n0 x n0, row-major, every entry a cotangent) of the dense block
+// from u_0 and xi_0: Kbar = L0^-T Phi(L0^T Lbar0) L0^-1.
+int dense_kbar(graphgp_graph_t g, graphgp_factor_t f, const float* u0, const float* xi0,
+               float sgn, float ldbar, float* Kbar, cudaStream_t s) {
+  int n0 = g->n0;
+  int64_t nn = (int64_t)n0 * n0;
+  Scratch sc(s);
+  float *P = nullptr, *T = nullptr;
+  GGP_TRY(sc.alloc(&P, nn));
+  GGP_TRY(sc.alloc(&T, nn));
+  unsigned grid = grid_for(nn, 256);
+  dense_lbar_kernel<<<grid, 256, 0, s>>>(u0, xi0, f->L0, n0, sgn, ldbar, Kbar);
+  dense_gemm_kernel<<<grid, 256, 0, s>>>(f->L0, Kbar, P, n0, 1, 1);     // Phi(L0^T Lbar0)
+  dense_gemm_kernel<<<grid, 256, 0, s>>>(f->L0inv, P, T, n0, 1, 0);     // L0^-T P
+  dense_gemm_kernel<<<grid, 256, 0, s>>>(T, f->L0inv, Kbar, n0, 0, 0);  // (L0^-T P) L0^-1
+  GGP_CUDA(cudaGetLastError());
+  return GRAPHGP_OK;
+}
+
+namespace {
+
 int dense_backward(graphgp_graph_t g, graphgp_factor_t f, const float* u0, const float* xi0,
                    float sgn, float ldbar, double* thetabar, cudaStream_t s) {
   int n0 = g->n0;
   int64_t nn = (int64_t)n0 * n0;
   Scratch sc(s);
-  float *Lb = nullptr, *P = nullptr, *T = nullptr;
+  float* Lb = nullptr;
   GGP_TRY(sc.alloc(&Lb, nn));
-  GGP_TRY(sc.alloc(&P, nn));
-  GGP_TRY(sc.alloc(&T, nn));
+  GGP_TRY(dense_kbar(g, f, u0, xi0, sgn, ldbar, Lb, s));
   unsigned grid = grid_for(nn, 256);
-  dense_lbar_kernel<<<grid, 256, 0, s>>>(u0, xi0, f->L0, n0, sgn, ldbar, Lb);
-  dense_gemm_kernel<<<grid, 256, 0, s>>>(f->L0, Lb, P, n0, 1, 1);      // Phi(L0^T Lbar0)
-  dense_gemm_kernel<<<grid, 256, 0, s>>>(f->L0inv, P, T, n0, 1, 0);    // L0^-T P
-  dense_gemm_kernel<<<grid, 256, 0, s>>>(T, f->L0inv, Lb, n0, 0, 0);   // (L0^-T P) L0^-1
   KernF kf = make_kernf(f->kern);
   switch (f->kern.type) {
     case GRAPHGP_MATERN12: dense_theta_kernel<GRAPHGP_MATERN12><<<grid, 256, 0, s>>>(Lb, g->xs, n0, kf, thetabar); break;

@@ -172,3 +172,22 @@ def test_autograd_functions_match_oracle(gpu_lib):
     tb3 = oracle.factor_backward(want["pts_pos"], want["nbr_pos"], k, 64, K, a3["bbar"],
                                  a3["bdbar"], a3["sigbar"])
     _theta_close(theta3.grad.numpy(), tb3)
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_nll_point_gradient(gpu_lib, case):
+    """dNLL/d(points) with the graph held fixed, against the oracle (itself
+    pinned by finite differences and by the invariances below); the GPU
+    result also sums to zero over the points (translation invariance)."""
+    kind, N, k, kern = case
+    g, f, want, fo, K = _setup(gpu_lib, kind, N, k, kern)
+    v = oracle.generate(fo, want["nbr_pos"], k, 64,
+                        workloads.white_noise(N, 63).astype(np.float64)).astype(np.float32)
+    pb_or = oracle.nll_grad_points(want, K, v.astype(np.float64))
+    pb = np_(gpu_lib.nll_backward_points(g, f, to_gpu(v))).astype(np.float64)
+    tol = _tol(want, kern, k)
+    assert rel_norm(pb, pb_or) < max(2e-3, 20 * tol)
+    assert np.all(np.abs(pb.sum(axis=0)) <= max(2e-3, 20 * tol) * np.abs(pb).sum())
+    # scaled cotangent
+    pb2 = np_(gpu_lib.nll_backward_points(g, f, to_gpu(v), nllbar=-0.5)).astype(np.float64)
+    assert rel_norm(pb2, -0.5 * pb) < 1e-6
