@@ -250,6 +250,14 @@ def differentiation_bench(stream, reps=3):
     b.record(stream)
     torch.cuda.synchronize()
     ms = a.elapsed_time(b) / reps
+    pbar = torch.empty((N, 3), dtype=torch.float32, device="cuda")
+    gg.nll_backward_points(g, f, v, out=pbar)
+    torch.cuda.synchronize()
+    a.record(stream)
+    gg.nll_backward_points(g, f, v, out=pbar)
+    b.record(stream)
+    torch.cuda.synchronize()
+    pts_ms = a.elapsed_time(b)
     t0 = time.perf_counter()
     f2 = gg.factor(g, kern)
     torch.cuda.synchronize()
@@ -258,6 +266,7 @@ def differentiation_bench(stream, reps=3):
     return {"workload": "differentiation: N=2^22 uniform [0,1]^3, k=32, squared exponential "
                         "l=0.03 nugget 1e-4; NLL + gradient (l, s2, nugget, v)",
             "nll_and_gradient_ms": ms, "points_per_s": N / (ms / 1e3),
+            "point_gradient_ms": pts_ms,
             "factor_ms": t_factor * 1e3, "status": st}
 
 
