@@ -11,14 +11,19 @@ graphgp_factor call) unless a Factor is passed in.
     xi  = whiten(graph, kernel_type, theta, v)         # xi = L^-1 v
     ld  = logdet(graph, kernel_type, theta)            # log det L L^T
     nll = nll(graph, kernel_type, theta, v)            # 0.5 xi.xi + 0.5 ld
+    nll = nll(graph, kernel_type, theta, v, points)    # also d/d points
+
+With `points` (the [N, d] tensor the graph was built from; its values are
+not read again) the NLL is also differentiable with respect to the point
+coordinates, the graph (order, neighbour lists, levels) held fixed.
 """
 from __future__ import annotations
 
 import torch
 
 from . import (Factor, Graph, Kernel, factor as _factor, generate_backward, logdet as _logdet,
-               nll as _nll, nll_backward, whiten_backward, generate as _generate,
-               whiten as _whiten)
+               nll as _nll, nll_backward, nll_backward_points, whiten_backward,
+               generate as _generate, whiten as _whiten)
 
 
 def _kernel(kernel_type: int, theta: torch.Tensor) -> Kernel:
@@ -97,6 +102,28 @@ class _Nll(torch.autograd.Function):
         return vbar, _theta_grad(tb, theta), None, None
 
 
+class _NllPoints(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, v, theta, points, graph, kernel_type):
+        f = _factor(graph, _kernel(kernel_type, theta))
+        out = _nll(graph, f, v.contiguous()).reshape(())
+        ctx.graph, ctx.fac = graph, f
+        ctx.save_for_backward(v, theta, points)
+        return out
+
+    @staticmethod
+    def backward(ctx, grad):
+        v, theta, points = ctx.saved_tensors
+        g = float(grad.item())
+        vbar, tb = nll_backward(ctx.graph, ctx.fac, v.contiguous(), g)
+        pbar = None
+        if ctx.needs_input_grad[2]:
+            d = points.shape[1]
+            pbar = nll_backward_points(ctx.graph, ctx.fac, v.contiguous(), g)[:, :d]
+            pbar = pbar.to(device=points.device, dtype=points.dtype)
+        return vbar, _theta_grad(tb, theta), pbar, None, None
+
+
 def generate(graph: Graph, kernel_type: int, theta: torch.Tensor, xi: torch.Tensor):
     return _Generate.apply(xi, theta, graph, kernel_type)
 
@@ -109,5 +136,10 @@ def logdet(graph: Graph, kernel_type: int, theta: torch.Tensor):
     return _Logdet.apply(theta, graph, kernel_type)
 
 
-def nll(graph: Graph, kernel_type: int, theta: torch.Tensor, v: torch.Tensor):
-    return _Nll.apply(v, theta, graph, kernel_type)
+def nll(graph: Graph, kernel_type: int, theta: torch.Tensor, v: torch.Tensor,
+        points: torch.Tensor | None = None):
+    if points is None:
+        return _Nll.apply(v, theta, graph, kernel_type)
+    if points.shape != (graph.N, points.shape[1]) or not 1 <= points.shape[1] <= 3:
+        raise ValueError("points must be the [N, d] tensor the graph was built from")
+    return _NllPoints.apply(v, theta, points, graph, kernel_type)

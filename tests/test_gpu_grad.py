@@ -191,3 +191,29 @@ def test_nll_point_gradient(gpu_lib, case):
     # scaled cotangent
     pb2 = np_(gpu_lib.nll_backward_points(g, f, to_gpu(v), nllbar=-0.5)).astype(np.float64)
     assert rel_norm(pb2, -0.5 * pb) < 1e-6
+
+
+def test_autograd_nll_with_points(gpu_lib):
+    """torch.autograd through the point-differentiable NLL: gradients with
+    respect to v, theta and the [N, 2] points the graph was built from (the
+    zero-padded third coordinate is dropped) against the oracle."""
+    from paper_2606_11402_gb300 import autograd as ga
+    N, k, kern = 2500, 8, (1, 1.0, 0.1, 1e-4)
+    pts2 = workloads.uniform_cube(N, 81)[:, :2].copy()
+    pts3 = np.concatenate([pts2, np.zeros((N, 1), np.float32)], axis=1)
+    want = oracle.build_graph(pts3, k, 64)
+    P = to_gpu(pts2).requires_grad_(True)
+    g = gpu_lib.build_graph(P.detach(), k, n0=64)
+    K = oracle.Kernel(*kern)
+    fo = oracle.factor(want["pts_pos"], want["nbr_pos"], k, 64, K)
+    v = oracle.generate(fo, want["nbr_pos"], k, 64,
+                        workloads.white_noise(N, 82).astype(np.float64)).astype(np.float32)
+    theta = torch.tensor([kern[2], kern[1], kern[3]], dtype=torch.float64, requires_grad=True)
+    vt = to_gpu(v).requires_grad_(True)
+    (2.0 * ga.nll(g, kern[0], theta, vt, P)).backward()
+    vbar_or, tb_or = oracle.nll_grad(want, K, v.astype(np.float64))
+    pb_or = oracle.nll_grad_points(want, K, v.astype(np.float64))
+    assert rel_norm(np_(vt.grad), 2.0 * vbar_or) < 1e-4
+    _theta_close(theta.grad.numpy(), 2.0 * tb_or)
+    assert P.grad.shape == (N, 2)
+    assert rel_norm(np_(P.grad), 2.0 * pb_or[:, :2]) < 2e-3
