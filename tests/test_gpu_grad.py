@@ -196,7 +196,11 @@ def test_nll_point_gradient(gpu_lib, case):
 def test_autograd_nll_with_points(gpu_lib):
     """torch.autograd through the point-differentiable NLL: gradients with
     respect to v, theta and the [N, 2] points the graph was built from (the
-    zero-padded third coordinate is dropped) against the oracle."""
+    zero-padded third coordinate is dropped).  The plumbing (order, the
+    upstream factor 2, the dropped coordinate) is checked against the direct
+    entry points to 1e-6; the values against the oracle within the FP32
+    conditioning bound of this cloud (2-D, smooth kernel: cond(K_cc) makes
+    the bound looser than 1e-4 here)."""
     from paper_2606_11402_gb300 import autograd as ga
     N, k, kern = 2500, 8, (1, 1.0, 0.1, 1e-4)
     pts2 = workloads.uniform_cube(N, 81)[:, :2].copy()
@@ -211,9 +215,16 @@ def test_autograd_nll_with_points(gpu_lib):
     theta = torch.tensor([kern[2], kern[1], kern[3]], dtype=torch.float64, requires_grad=True)
     vt = to_gpu(v).requires_grad_(True)
     (2.0 * ga.nll(g, kern[0], theta, vt, P)).backward()
+    assert P.grad.shape == (N, 2)
+    f = gpu_lib.factor(g, gpu_lib.Kernel(*kern))
+    vb, tb = gpu_lib.nll_backward(g, f, to_gpu(v))
+    pb = gpu_lib.nll_backward_points(g, f, to_gpu(v))
+    assert rel_norm(np_(vt.grad), 2.0 * np_(vb)) < 1e-6
+    assert np.allclose(theta.grad.numpy(), 2.0 * np_(tb), rtol=1e-6, atol=0.0)
+    assert rel_norm(np_(P.grad), 2.0 * np_(pb)[:, :2]) < 1e-6
     vbar_or, tb_or = oracle.nll_grad(want, K, v.astype(np.float64))
     pb_or = oracle.nll_grad_points(want, K, v.astype(np.float64))
-    assert rel_norm(np_(vt.grad), 2.0 * vbar_or) < 1e-4
-    _theta_close(theta.grad.numpy(), 2.0 * tb_or)
-    assert P.grad.shape == (N, 2)
-    assert rel_norm(np_(P.grad), 2.0 * pb_or[:, :2]) < 2e-3
+    tol = fp32_tolerance(want, kern)[0]
+    assert rel_norm(np_(vt.grad), 2.0 * vbar_or) < tol
+    _theta_close(theta.grad.numpy(), 2.0 * tb_or, tol)
+    assert rel_norm(np_(P.grad), 2.0 * pb_or[:, :2]) < max(2e-3, 20 * tol)
