@@ -510,7 +510,10 @@ def run_ours(args):
         "e2e": {"value": e2e_value, "unit": UNIT, "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": 4 * N, "d2h_bytes_per_step": 8 * N + 8,
                 "copies": "pinned host buffers, own streams, overlapping neighbouring steps"},
-        "gpu_launches": 4 * args.steps,
+        # per step: generate = dense mat-vec + the two single-block runs of
+        # small levels + the cooperative level sweep; whiten = dense mat-vec +
+        # tile sweep; logdet is a device-to-device copy of the factor's sum
+        "gpu_launches": 6 * args.steps,
         "clocks": _clock_summary(os.path.join("/tmp", f"ggp_clocks_{rank}.csv"), local),
     }
     if diff is not None:

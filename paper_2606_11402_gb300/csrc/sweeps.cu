@@ -4,11 +4,15 @@
 // generate: v_0 = L0 xi_0 for the dense block, then batch by batch
 // (Sec. 2.2: points of one depth level are conditionally independent)
 // v_i = b_i . v_c(i) + sigma_i xi_i; every neighbour lies in an earlier level.
-// One cooperative launch walks all levels with a grid-wide barrier between
+// One cooperative launch walks the levels with a grid-wide barrier between
 // consecutive levels (sweepsync.cuh).  Rows, sigma and xi do not depend on
 // the field: each lane group loads those of its next step before gathering
 // the current one, and those of a level's first step before the barrier, so
-// the row stream overlaps both the gathers and the barrier.
+// the row stream overlaps both the gathers and the barrier.  The depth levels
+// at both ends of the sweep hold a few dozen to a few hundred points (about
+// 90 levels at any N); each of those runs is done by a single block that
+// synchronises with __syncthreads, since a grid barrier per level costs
+// more than the level's work there.
 //
 // whiten: xi_i = (v_i - b_i . v_c(i)) / sigma_i has no dependencies.  Blocks
 // walk spatial tiles through every level (plus xi_0 = L0^-1 v_0 for the
@@ -105,21 +109,28 @@ constexpr int kSweepThreads = 256;
 // two row buffers below about 64 registers.
 __host__ __device__ constexpr int gen_steps(int hp) { return hp <= 4 ? 4 : (hp <= 8 ? 2 : 1); }
 
-// LANES threads share one position: lane h holds entries [h HP, (h+1) HP) of
-// the row (HP = KP / LANES) and the partial sums meet in shuffles.  A lane
-// group takes U positions per step, and the rows, sigma and xi of its next
-// step are loaded before the gathers of the current one, so their DRAM
-// latency hides under the gathers.  The first step of a level is loaded
-// before the level barrier (rows do not depend on the field).
-template <int KP, int LANES, int U>
-__global__ void __launch_bounds__(kSweepThreads) generate_kernel(
-    const int32_t* __restrict__ nbr, const float* __restrict__ b, const float* __restrict__ sigma,
-    const float* __restrict__ xi, float* v, const int64_t* __restrict__ level_off,
-    int num_levels, int64_t n0, LevelBarrier lb) {
-  constexpr int HP = KP / LANES;                // row entries per lane
-  constexpr int GPB = kSweepThreads / LANES;    // lane groups per block
-  constexpr int PPB = U * GPB;                  // positions per block step
-  __shared__ int s_flag;
+// Levels [l_first, l_end) of generate.  LANES threads share one position:
+// lane h holds entries [h HP, (h+1) HP) of the row (HP = KP / LANES) and the
+// partial sums meet in shuffles.  A lane group takes U positions per step,
+// and the rows, sigma and xi of its next step are loaded before the gathers
+// of the current one, so their DRAM latency hides under the gathers.  The
+// first step of a level is loaded before the level's wait (rows do not depend
+// on the field).
+//   GRID: a cooperative launch; block b takes the b-th of gridDim.x equal
+//         slices of every level and waits at the grid-wide level barrier.
+//   !GRID: one block takes whole levels and waits at __syncthreads (levels
+//         of a few hundred points, where the grid barrier would dominate).
+template <int KP, int LANES, int U, int NT, bool GRID>
+__device__ __forceinline__ void gen_levels(const int32_t* __restrict__ nbr,
+                                           const float* __restrict__ b,
+                                           const float* __restrict__ sigma,
+                                           const float* __restrict__ xi, float* v,
+                                           const int64_t* __restrict__ level_off, int l_first,
+                                           int l_end, int64_t n0, const LevelBarrier& lb,
+                                           int* s_flag) {
+  constexpr int HP = KP / LANES;   // row entries per lane
+  constexpr int GPB = NT / LANES;  // lane groups per block
+  constexpr int PPB = U * GPB;     // positions per block step
   const uint64_t pol_rows = l2_evict_first();
   const uint64_t pol_v = l2_evict_last();
   const int h = threadIdx.x % LANES;
@@ -128,11 +139,14 @@ __global__ void __launch_bounds__(kSweepThreads) generate_kernel(
   const float* bw = b + h * HP;
   Row<HP> rn[U];
   float sgn[U], xn[U];
-  for (int l = 1; l < num_levels; l++) {
+  for (int l = l_first; l < l_end; l++) {
     const int64_t lo = level_off[l], n = level_off[l + 1] - lo;
-    const int64_t per = (n + gridDim.x - 1) / gridDim.x;
-    const int64_t b0 = lo + min((int64_t)blockIdx.x * per, n);
-    const int64_t hi = lo + min((int64_t)(blockIdx.x + 1) * per, n);
+    int64_t b0 = lo, hi = lo + n;
+    if (GRID) {
+      const int64_t per = (n + gridDim.x - 1) / gridDim.x;
+      b0 = lo + min((int64_t)blockIdx.x * per, n);
+      hi = lo + min((int64_t)(blockIdx.x + 1) * per, n);
+    }
     int64_t p = b0 + slot;
 #pragma unroll
     for (int u = 0; u < U; u++) {
@@ -146,7 +160,13 @@ __global__ void __launch_bounds__(kSweepThreads) generate_kernel(
         }
       }
     }
-    if (l > 1 && lb.wait(l - 1, gridDim.x, &s_flag)) return;
+    if (l > l_first) {
+      if (GRID) {
+        if (lb.wait(l - 1, gridDim.x, s_flag)) return;
+      } else {
+        __syncthreads();
+      }
+    }
     const int64_t steps = (hi - b0 + PPB - 1) / PPB;
     for (int64_t st = 0; st < steps; st++) {
       Row<HP> r[U];
@@ -184,9 +204,36 @@ __global__ void __launch_bounds__(kSweepThreads) generate_kernel(
       }
       p = pn;
     }
-    __syncthreads();
-    lb.arrive(l);
+    if (GRID) {
+      __syncthreads();
+      lb.arrive(l);
+    }
   }
+}
+
+template <int KP, int LANES, int U>
+__global__ void __launch_bounds__(kSweepThreads) generate_kernel(
+    const int32_t* __restrict__ nbr, const float* __restrict__ b, const float* __restrict__ sigma,
+    const float* __restrict__ xi, float* v, const int64_t* __restrict__ level_off, int l_first,
+    int l_end, int64_t n0, LevelBarrier lb) {
+  __shared__ int s_flag;
+  gen_levels<KP, LANES, U, kSweepThreads, true>(nbr, b, sigma, xi, v, level_off, l_first, l_end,
+                                                n0, lb, &s_flag);
+}
+
+// One block of small_threads(KP) threads for runs of small levels.
+__host__ __device__ constexpr int small_threads(int hp) { return hp <= 4 ? 1024 : (hp <= 8 ? 512 : 256); }
+__host__ __device__ constexpr int small_steps(int hp) { return hp <= 8 ? 2 : 1; }
+
+template <int KP, int LANES>
+__global__ void __launch_bounds__(small_threads(KP / LANES), 1) generate_small_kernel(
+    const int32_t* __restrict__ nbr, const float* __restrict__ b, const float* __restrict__ sigma,
+    const float* __restrict__ xi, float* v, const int64_t* __restrict__ level_off, int l_first,
+    int l_end, int64_t n0) {
+  constexpr int HP = KP / LANES;
+  LevelBarrier none{nullptr, nullptr, 0};
+  gen_levels<KP, LANES, small_steps(HP), small_threads(HP), false>(
+      nbr, b, sigma, xi, v, level_off, l_first, l_end, n0, none, nullptr);
 }
 
 template <int KP>
@@ -323,25 +370,47 @@ __global__ void nll_finish_kernel(const double* __restrict__ sq, const double* _
 template <int KP>
 int launch_generate(graphgp_graph_t g, graphgp_factor_t f, const float* xi, float* v,
                     cudaStream_t s) {
-  if (g->num_levels <= 1) return GRAPHGP_OK;
-  GGP_CUDA(cudaMemsetAsync(g->level_bar, 0, g->num_levels * sizeof(uint32_t), s));
-  constexpr int LANES = gen_lanes(KP), U = gen_steps(KP / LANES);
-  auto kern = generate_kernel<KP, LANES, U>;
-  static int max_grid = 0;
-  if (!max_grid) max_grid = coop_grid(kern, kSweepThreads);
-  int64_t want = (g->max_level_size + kSweepThreads - 1) / kSweepThreads;
-  int grid = (int)std::min<int64_t>(max_grid, std::max<int64_t>(want, 1));
-  LevelBarrier lb{g->level_bar, g->err, g->max_spin};
-  const int32_t* nbr = g->nbr;
-  const float* bw = f->b;
-  const float* sg = f->sigma;
-  const int64_t* lo = g->level_off_d;
-  int nl = g->num_levels;
+  const int L = g->num_levels;
+  if (L <= 1) return GRAPHGP_OK;
+  constexpr int LANES = gen_lanes(KP), HP = KP / LANES, U = gen_steps(HP);
+  // Runs of small levels at both ends of the sweep (a level that one block
+  // covers in two steps) go to one block; the levels between them to the
+  // cooperative grid.  Levels [1, a) and [z, L) are small.
+  constexpr int64_t kSmall = 2 * small_steps(HP) * (small_threads(HP) / LANES);
+  const std::vector<int64_t>& lo = g->level_off_h;
+  int a = 1;
+  while (a < L && lo[a + 1] - lo[a] <= kSmall) a++;
+  int z = L;
+  while (z > a && lo[z] - lo[z - 1] <= kSmall) z--;
+  const int64_t* lod = g->level_off_d;
   int64_t n0 = g->n0;
-  void* args[] = {(void*)&nbr, (void*)&bw, (void*)&sg, (void*)&xi, (void*)&v,
-                  (void*)&lo,  (void*)&nl, (void*)&n0, (void*)&lb};
-  GGP_CUDA(cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(kSweepThreads), args, 0,
-                                       s));
+  constexpr int NTS = small_threads(HP);
+  if (a > 1) {
+    generate_small_kernel<KP, LANES><<<1, NTS, 0, s>>>(g->nbr, f->b, f->sigma, xi, v, lod, 1, a,
+                                                       n0);
+    GGP_CUDA(cudaGetLastError());
+  }
+  if (a < z) {
+    GGP_CUDA(cudaMemsetAsync(g->level_bar, 0, L * sizeof(uint32_t), s));
+    auto kern = generate_kernel<KP, LANES, U>;
+    static int max_grid = 0;
+    if (!max_grid) max_grid = coop_grid(kern, kSweepThreads);
+    int64_t want = (g->max_level_size + kSweepThreads - 1) / kSweepThreads;
+    int grid = (int)std::min<int64_t>(max_grid, std::max<int64_t>(want, 1));
+    LevelBarrier lb{g->level_bar, g->err, g->max_spin};
+    const int32_t* nbr = g->nbr;
+    const float* bw = f->b;
+    const float* sg = f->sigma;
+    void* args[] = {(void*)&nbr, (void*)&bw, (void*)&sg, (void*)&xi, (void*)&v,
+                    (void*)&lod, (void*)&a,  (void*)&z,  (void*)&n0, (void*)&lb};
+    GGP_CUDA(cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(kSweepThreads), args,
+                                         0, s));
+  }
+  if (z < L) {
+    generate_small_kernel<KP, LANES><<<1, NTS, 0, s>>>(g->nbr, f->b, f->sigma, xi, v, lod, z, L,
+                                                       n0);
+    GGP_CUDA(cudaGetLastError());
+  }
   return GRAPHGP_OK;
 }
 
