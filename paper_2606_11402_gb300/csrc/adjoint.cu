@@ -163,6 +163,100 @@ __global__ void whiten_transpose_kernel(const int64_t* __restrict__ rowptr,
   }
 }
 
+// The same transposed gather for the sparse positions, walking the spatial
+// tiles of the whiten sweep: a block takes one tile (a k-d in-order rank
+// range) through every level >= 1.  The children of a point are its spatial
+// neighbours in deeper levels, so their cotangents, sigmas and rows are those
+// of the same tile, about 290 KB per tile at k = 16.  One block of 1024
+// threads per SM keeps 152 tiles in flight (~45 MB, inside L2), so a row is
+// fetched from DRAM about once although each of its k entries is read by a
+// different parent; with 256-thread blocks and 8 tiles per SM the tiles in
+// flight outgrew L2 and the rows were fetched again for every parent.  The
+// entries of a position are read four at a time before their products are
+// added, in list order, so the arithmetic per position is that of
+// whiten_transpose_kernel.
+constexpr int kTransposeThreads = 1024;
+
+__device__ __forceinline__ int32_t tile_level_prefix(const int32_t* __restrict__ ts, int num_levels,
+                                                     int32_t* s_start, int32_t* s_pref,
+                                                     int32_t* s_carry, int32_t* wsum) {
+  if (threadIdx.x == 0) *s_carry = 0;
+  __syncthreads();
+  for (int base = 1; base < num_levels; base += blockDim.x) {
+    const int l = base + threadIdx.x;
+    int32_t c = 0;
+    if (l < num_levels) {
+      const int32_t a0 = ts[l];
+      c = ts[num_levels + l] - a0;
+      s_start[l] = a0;
+    }
+    int32_t x = c;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if ((threadIdx.x & 31) >= o) x += y;
+    }
+    if ((threadIdx.x & 31) == 31) wsum[threadIdx.x >> 5] = x;
+    __syncthreads();
+    int32_t wpre = 0;
+    for (int w = 0; w < (int)(threadIdx.x >> 5); w++) wpre += wsum[w];
+    const int32_t carry = *s_carry;
+    if (l < num_levels) s_pref[l] = carry + wpre + x - c;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) *s_carry = carry + wpre + x;
+    __syncthreads();
+  }
+  return *s_carry;
+}
+
+__global__ void __launch_bounds__(kTransposeThreads, 1) whiten_transpose_tiles_kernel(
+    const int64_t* __restrict__ rowptr, const int32_t* __restrict__ cedge, int kp, int64_t n0,
+    const float* __restrict__ b, const float* __restrict__ sigma, const float* __restrict__ xibar,
+    float* __restrict__ vbar, const int32_t* __restrict__ tile_start, int64_t n_tiles,
+    int num_levels) {
+  extern __shared__ int32_t sm[];
+  int32_t* s_start = sm;              // [num_levels]
+  int32_t* s_pref = sm + num_levels;  // [num_levels + 1]
+  __shared__ int32_t s_carry;
+  __shared__ int32_t wsum[kTransposeThreads / 32];
+  for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+    const int32_t total = tile_level_prefix(tile_start + t * num_levels, num_levels, s_start,
+                                            s_pref, &s_carry, wsum);
+    for (int32_t vi = threadIdx.x; vi < total; vi += blockDim.x) {
+      int lo = 1, hi = num_levels - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (s_pref[mid] <= vi) lo = mid; else hi = mid - 1;
+      }
+      const int64_t p = (int64_t)s_start[lo] + (vi - s_pref[lo]);
+      float acc = xibar[p] / sigma[p];
+      int64_t e = rowptr[p];
+      const int64_t e1 = rowptr[p + 1];
+      for (; e + 4 <= e1; e += 4) {
+        int32_t c[4];
+        float x[4], sg[4], w[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) c[q] = cedge[e + q];
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+          const int64_t j = c[q] / kp + n0;
+          x[q] = xibar[j];
+          sg[q] = sigma[j];
+          w[q] = b[c[q]];
+        }
+#pragma unroll
+        for (int q = 0; q < 4; q++) acc = fmaf(-(x[q] / sg[q]), w[q], acc);
+      }
+      for (; e < e1; e++) {
+        const int32_t ce = cedge[e];
+        const int64_t j = ce / kp + n0;
+        acc = fmaf(-(xibar[j] / sigma[j]), b[ce], acc);
+      }
+      vbar[p] = acc;
+    }
+    __syncthreads();
+  }
+}
+
 // ---- generate VJP: reverse level sweep, deepest level first, one cooperative
 // launch with a grid barrier between levels (children of a level-l row are in
 // deeper levels, all complete once level l+1 is) ----------------------------------
@@ -709,9 +803,21 @@ int run_whiten_backward(graphgp_graph_t g, graphgp_factor_t f, const float* v, c
   dense_lower_tmatvec_kernel<<<(n0 + 255) / 256, 256, 0, s>>>(f->L0inv, xibar, vbar, n0);
   GGP_CUDA(cudaGetLastError());
   GGP_TRY(dense_backward(g, f, vbar, xi, -1.0f, (float)logdetbar, thetabar, s));
-  whiten_transpose_kernel<<<grid_for(g->N, 256), 256, 0, s>>>(g->csr.rowptr, g->csr.child, g->kp,
-                                                              n0, f->b, f->sigma, xibar, vbar,
-                                                              g->N);
+  if (g->tile_start && g->num_levels <= 8192 && g->N > n0) {
+    // dense positions in position order, the sparse ones tile by tile
+    whiten_transpose_kernel<<<grid_for(n0, 256), 256, 0, s>>>(g->csr.rowptr, g->csr.child, g->kp,
+                                                              n0, f->b, f->sigma, xibar, vbar, n0);
+    GGP_CUDA(cudaGetLastError());
+    const size_t smem = (2 * (size_t)g->num_levels + 1) * sizeof(int32_t);
+    const int64_t grid = std::min<int64_t>(g->n_tiles, num_sms());
+    whiten_transpose_tiles_kernel<<<(unsigned)grid, kTransposeThreads, smem, s>>>(
+        g->csr.rowptr, g->csr.child, g->kp, n0, f->b, f->sigma, xibar, vbar, g->tile_start,
+        g->n_tiles, g->num_levels);
+  } else {
+    whiten_transpose_kernel<<<grid_for(g->N, 256), 256, 0, s>>>(g->csr.rowptr, g->csr.child,
+                                                                g->kp, n0, f->b, f->sigma, xibar,
+                                                                vbar, g->N);
+  }
   GGP_CUDA(cudaGetLastError());
   GGP_TRY(factor_backward(g, f, 0, xibar, (float)(2.0 * logdetbar), v, xi, nullptr, thetabar, s));
   return GRAPHGP_OK;
