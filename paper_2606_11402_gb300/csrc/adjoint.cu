@@ -809,6 +809,7 @@ int run_whiten_backward(graphgp_graph_t g, graphgp_factor_t f, const float* v, c
                                                               n0, f->b, f->sigma, xibar, vbar, n0);
     GGP_CUDA(cudaGetLastError());
     const size_t smem = (2 * (size_t)g->num_levels + 1) * sizeof(int32_t);
+    GGP_CUDA(allow_dyn_smem(whiten_transpose_tiles_kernel, smem));
     const int64_t grid = std::min<int64_t>(g->n_tiles, num_sms());
     whiten_transpose_tiles_kernel<<<(unsigned)grid, kTransposeThreads, smem, s>>>(
         g->csr.rowptr, g->csr.child, g->kp, n0, f->b, f->sigma, xibar, vbar, g->tile_start,

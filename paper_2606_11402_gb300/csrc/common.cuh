@@ -239,6 +239,16 @@ inline int num_sms() {
   return n;
 }
 
+// Kernels whose dynamic shared memory grows with the number of depth levels
+// (two int32 per level in the tile walks): above the 48 KB a launch gets by
+// default the kernel must opt in, up to the 227 KB of one block.
+template <class F>
+inline cudaError_t allow_dyn_smem(F fn, size_t smem) {
+  if (smem <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)smem);
+}
+
 inline unsigned grid_for(int64_t n, int block, int64_t cap_per_sm = 32) {
   int64_t g = (n + block - 1) / block;
   int64_t cap = (int64_t)num_sms() * cap_per_sm;

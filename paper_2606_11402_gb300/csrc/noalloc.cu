@@ -193,6 +193,7 @@ template <int KP>
 int launch_tiles(graphgp_graph_t g, graphgp_factor_t f, const float* v, double* slot,
                  cudaStream_t s) {
   size_t smem = (2 * (size_t)g->num_levels + 1) * sizeof(int32_t);
+  GGP_CUDA(allow_dyn_smem(nll_tiles_slot_kernel<KP>, smem));
   int per_sm = 0;
   GGP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, nll_tiles_slot_kernel<KP>, 256,
                                                          smem));

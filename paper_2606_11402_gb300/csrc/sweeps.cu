@@ -421,6 +421,7 @@ int launch_whiten(graphgp_graph_t g, graphgp_factor_t f, const float* v, float* 
   if (n <= 0) return GRAPHGP_OK;
   if (g->tile_start && g->num_levels <= 8192) {
     size_t smem = (2 * (size_t)g->num_levels + 1) * sizeof(int32_t);
+    GGP_CUDA(allow_dyn_smem(whiten_tiles_kernel<KP>, smem));
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, whiten_tiles_kernel<KP>, 256, smem);
     int64_t grid = std::min<int64_t>(g->n_tiles, (int64_t)std::max(per_sm, 1) * num_sms());
