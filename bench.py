@@ -270,6 +270,16 @@ def differentiation_bench(stream, reps=3):
             "factor_ms": t_factor * 1e3, "status": st}
 
 
+def headline_config(N=1 << 26, k=16, n0=256, world=1):
+    """The benchmark workload, as both arms name it in their JSON line."""
+    lg = N.bit_length() - 1
+    size = f"2^{lg}" if N == 1 << lg else str(N)
+    return {"workload": (f"metric: unit Gaussian 3-D cloud, N={size}, k={k}, Matern-3/2 "
+                         f"s2=1 l=0.1 nugget 1e-6, n0={n0}; step = generate + whiten + logdet"),
+            "N": N, "k": k, "n0": n0, "l2": "inputs larger than L2 (no flush)",
+            "parallelism": "replicas" if world > 1 else "single GPU"}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -280,8 +290,7 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": cb["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "metric: unit Gaussian 3-D, N=2^26 (sampled), k=16, "
-                                   "Matern-3/2 l=0.1 nugget 1e-6, n0=256"},
+            "config": dict(headline_config(), sample=cb["sample"]),
             "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
             "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -488,11 +497,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": ("metric: unit Gaussian 3-D cloud, N=2^26, k=16, Matern-3/2 "
-                                "s2=1 l=0.1 nugget 1e-6, n0=256; step = generate + whiten + logdet"),
-                   "N": N, "k": k, "n0": g.n0, "levels": g.num_levels,
-                   "l2": "inputs larger than L2 (no flush)",
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "config": dict(headline_config(N, k, g.n0, world), levels=g.num_levels),
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm,
                      "unit": "GB/s", "frac": achieved / hbm,
                      "traffic": _measured_traffic(
