@@ -116,7 +116,8 @@ def poisson_stream(n_inst: int, rate: float, duration: float, seed: int,
 def _percentiles(lat):
     a = np.asarray(lat)
     return dict(p50_ms=float(np.percentile(a, 50) * 1e3), p99_ms=float(np.percentile(a, 99) * 1e3),
-                mean_ms=float(a.mean() * 1e3), max_ms=float(a.max() * 1e3))
+                p999_ms=float(np.percentile(a, 99.9) * 1e3), mean_ms=float(a.mean() * 1e3),
+                max_ms=float(a.max() * 1e3))
 
 
 def run_stream(reqs, inputs, server: Server | None = None, instances=None, stream=None):

@@ -43,7 +43,7 @@ def test_poisson_stream_is_seeded():
 
 
 def test_latency_percentiles():
-    """p50 / p99 / mean / max in milliseconds of latencies given in seconds,
+    """p50 / p99 / p99.9 / mean / max in milliseconds of latencies given in seconds,
     against the order statistics of 1..100 ms (linear interpolation)."""
     lat = np.arange(1, 101) * 1e-3
     rng = np.random.default_rng(0)
@@ -51,5 +51,6 @@ def test_latency_percentiles():
     p = sv._percentiles(lat)
     assert np.isclose(p["p50_ms"], 50.5)
     assert np.isclose(p["p99_ms"], 99.01)
+    assert np.isclose(p["p999_ms"], 99.901)
     assert np.isclose(p["mean_ms"], 50.5)
     assert np.isclose(p["max_ms"], 100.0)
