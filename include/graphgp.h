@@ -69,6 +69,19 @@ typedef struct {
   double sigma2;      /* marginal variance s2 > 0 */
   double lengthscale; /* l > 0 */
   double nugget;      /* >= 0, added on the diagonal */
+  double rescue_tol;  /* precision policy of the per-point conditionals (not
+                         in the paper, which runs one precision).  Every
+                         conditional is factored in FP32; its relative error
+                         is estimated a priori as
+                           est = 2^-24 (K_00 / p_min) (K_00 / sigma_i^2)
+                         (p_min = smallest Cholesky pivot of K_cc; K_00 / p_min
+                         bounds cond(K_cc) from below, K_00 / sigma^2 is the
+                         cancellation in sigma^2 = K_ii - K_ic b).  A row with
+                         est > rescue_tol, a floored pivot or a non-finite
+                         result is recomputed in FP64.  0 = default 2^-6;
+                         < 0 = every conditional in FP64 (slow on GB300:
+                         FP64 runs at 1/64 of the FP32 rate).  Must be
+                         finite. */
 } graphgp_kernel;
 
 typedef struct {
@@ -304,6 +317,12 @@ void graphgp_server_destroy(graphgp_server_t sv);
  * Synchronises `stream`.  Returns GRAPHGP_ERR_TIMEOUT when the waits gave up
  * and recorded the timeout as designed (the context stays usable). */
 int graphgp_selftest_wait_timeout(int64_t max_spin, void* stream);
+
+/* Writes the compute capability the library's device code was loaded for
+ * (cudaFuncAttributes::binaryVersion of one of its kernels: major*10+minor,
+ * 103 on GB300).  Not a paper operation.  Loads the module on the current
+ * device if needed. */
+int graphgp_binary_version(int* version);
 
 const char* graphgp_status_string(int status);
 

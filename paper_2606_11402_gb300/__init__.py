@@ -37,7 +37,7 @@ class GraphGPError(RuntimeError):
 class _Kernel(ctypes.Structure):
     _fields_ = [("type", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("sigma2", ctypes.c_double), ("lengthscale", ctypes.c_double),
-                ("nugget", ctypes.c_double)]
+                ("nugget", ctypes.c_double), ("rescue_tol", ctypes.c_double)]
 
 
 class _BuildOpts(ctypes.Structure):
@@ -52,10 +52,13 @@ class Kernel:
     sigma2: float = 1.0
     lengthscale: float = 0.1
     nugget: float = 0.0
+    # rows whose a-priori FP32 error estimate exceeds this are recomputed in
+    # FP64 (0 = library default 2^-6, negative = every row in FP64)
+    rescue_tol: float = 0.0
 
     def _c(self) -> _Kernel:
         return _Kernel(int(self.type), 0, float(self.sigma2), float(self.lengthscale),
-                       float(self.nugget))
+                       float(self.nugget), float(self.rescue_tol))
 
 
 _lib = None
@@ -94,6 +97,7 @@ def load() -> ctypes.CDLL:
             "graphgp_nll_backward": [_P, _P, _P, ctypes.c_double, _P, _P, _P],
             "graphgp_nll_backward_points": [_P, _P, _P, ctypes.c_double, _P, _P],
             "graphgp_selftest_wait_timeout": [_I64, _P],
+            "graphgp_binary_version": [_P],
             "graphgp_generate_fused": [_P, _P, _P, _P, _P, _P],
             "graphgp_whiten_fused": [_P, _P, _P, _P, _P, _P, _P],
             "graphgp_nll_fused": [_P, _P, _P, _P, _P, _P],
@@ -349,6 +353,13 @@ def nll_fused(graph: Graph, kernel: Kernel, v: torch.Tensor, out: torch.Tensor |
                                     _opt(not_pd, torch.int64, 1, "not_pd"), _stream(stream)),
            "nll_fused")
     return o
+
+
+def binary_version() -> int:
+    """Compute capability (major * 10 + minor) of the loaded device code."""
+    v = ctypes.c_int(0)
+    _check(load().graphgp_binary_version(ctypes.byref(v)), "binary_version")
+    return v.value
 
 
 def selftest_wait_timeout(max_spin: int = 20000, stream=None) -> int:

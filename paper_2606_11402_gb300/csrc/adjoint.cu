@@ -394,7 +394,7 @@ __global__ void __launch_bounds__(128) factor_backward_kernel(
     // above are discarded and the row goes to factor_backward_rescue_kernel
     const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (grp * G));
     const bool lane_bad = real && !isfinite(st.b_own);
-    const bool rescue = st.clamped || !(st.min_piv >= kRescuePivot * (kf.s2 + kf.nug)) ||
+    const bool rescue = st.clamped || row_error_too_large(st.max_ratio, st.varw, st.sigma, kf) ||
                         !isfinite(st.sigma) || (__ballot_sync(full, lane_bad) & gmask);
     if (valid && a == 0) {
       if (rescue) {
@@ -448,7 +448,7 @@ __global__ void __launch_bounds__(128) factor_backward_wide_kernel(
     const float sbar = sigbar / (2.0f * sigma);
     for (int a = lane; a < k; a += 32) W.g[a] = alpha * v[row[a]];
     __syncwarp();
-    wide_chol_solve(W, k);
+    wide_chol_solve(W, k, r.inc);
     for (int a = lane; a < k; a += 32) {
       const float ga = W.g[a], ba = W.y[a];
       const float4 xa = W.x[a];
@@ -570,7 +570,7 @@ __global__ void __launch_bounds__(128) factor_backward_thread_kernel(
     }
 #pragma unroll
     for (int a = 0; a < K; a++) g[a] = a < k ? alpha * v[ca[a]] : 0.0f;
-    thread_chol_solve<K>(p, g);
+    thread_chol_solve<K>(p, k, g);
     const float* bb = p.y;
     // row sums in FP32 (at most k + 1 terms), added to the FP64 totals
     ts += sbar;  // Kbar_ii = sbar

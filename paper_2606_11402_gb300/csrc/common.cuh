@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
 #include <cstdio>
 #include <vector>
 
@@ -171,8 +172,13 @@ namespace ggp {
 // ---------------------------------------------------------------------------
 struct KernF {
   float s2, inv_ell, nug;
+  float resc_T;            // FP64 rescue threshold of the row-error estimate x 2^24, rescue.cuh
   double s2d, elld, nugd;  // the same parameters in FP64 (rescue path)
 };
+
+// Default per-row error estimate above which a conditional is recomputed in
+// FP64 (rescue.cuh): 2^-6.
+constexpr double kDefaultRescueTol = 0.015625;
 
 template <int KT>
 __device__ __forceinline__ float kappa_d2(const KernF& p, float d2) {
@@ -190,6 +196,81 @@ __device__ __forceinline__ float kappa_d2(const KernF& p, float d2) {
       return p.s2 * (1.0f + a + a * a * (1.0f / 3.0f)) * expf(-a);
     }
   }
+}
+
+// Variogram gamma(r) = kappa(0) - kappa(r) (nugget excluded) from the squared
+// distance, in FP32 with a small relative error all the way down to r -> 0,
+// where kappa(r) is close to kappa(0) and 1 - kappa(r)/kappa(0) computed from
+// kappa would keep none of its digits.  The increment form of the per-point
+// factors (pointfactor.cuh) is built from these values.  Below a switch point
+// gamma comes from a series with positive terms (or alternating terms of
+// decreasing size), above it from the closed form, which there loses at most
+// a small factor to cancellation:
+//   SE (u = r^2 / 2l^2), Matern-1/2 (u = r/l), u < 1/2:
+//       1 - e^-u = u (1 - u/2 + u^2/6 - ...)            (closed form: <= 2.6x)
+//   Matern-3/2, a = sqrt3 r/l < 1:
+//       1 - (1 + a) e^-a = e^-a sum_{n>=2} a^n/n!       (closed form: <= 2.8x)
+//   Matern-5/2, a = sqrt5 r/l < 2:
+//       1 - (1 + a + a^2/3) e^-a = e^-a (a^2/6 + sum_{n>=3} a^n/n!)  (<= 2.4x)
+// The series are cut where their remainder falls below 2^-28 of the value.
+__host__ __device__ constexpr double inv_factorial(int n) {
+  return n <= 1 ? 1.0 : inv_factorial(n - 1) / n;
+}
+
+// sum_{n=N..NMAX} a^(n-N) / n!, Horner with compile-time coefficients.
+template <int N, int NMAX>
+__device__ __forceinline__ float exp_tail_series(float a) {
+  constexpr float c = (float)inv_factorial(N);
+  if constexpr (N == NMAX) {
+    return c;
+  } else {
+    return fmaf(exp_tail_series<N + 1, NMAX>(a), a, c);
+  }
+}
+
+// sum_{n=N..NMAX} (-1)^(n-N) u^(n-N) / n!
+template <int N, int NMAX>
+__device__ __forceinline__ float exp_alt_series(float u) {
+  constexpr float c = (float)inv_factorial(N);
+  if constexpr (N == NMAX) {
+    return c;
+  } else {
+    return fmaf(-exp_alt_series<N + 1, NMAX>(u), u, c);
+  }
+}
+
+struct KG {
+  float k, g;  // kappa(r), gamma(r)
+};
+
+// kappa and gamma from one exponential (the per-point factors pick one of
+// the two per row).  The closed form of gamma is used at and above the
+// switch point, the series below it.
+template <int KT>
+__device__ __forceinline__ KG kappa_gamma_d2(const KernF& p, float d2) {
+  if (KT == GRAPHGP_SQEXP || KT == GRAPHGP_MATERN12) {
+    const float u = KT == GRAPHGP_SQEXP ? 0.5f * d2 * p.inv_ell * p.inv_ell : sqrtf(d2) * p.inv_ell;
+    const float e = expf(-u);
+    return KG{p.s2 * e, p.s2 * (u < 0.5f ? u * exp_alt_series<1, 11>(u) : 1.0f - e)};
+  } else if (KT == GRAPHGP_MATERN32) {
+    const float a = 1.7320508075688772f * sqrtf(d2) * p.inv_ell;
+    const float e = expf(-a);
+    const float pe = (1.0f + a) * e;
+    return KG{p.s2 * pe, p.s2 * (a < 1.0f ? a * a * fmaf(a, exp_tail_series<3, 12>(a), 0.5f) * e
+                                           : 1.0f - pe)};
+  } else {
+    const float a = 2.2360679774997896f * sqrtf(d2) * p.inv_ell;
+    const float e = expf(-a);
+    const float pe = (1.0f + a + a * a * (1.0f / 3.0f)) * e;
+    return KG{p.s2 * pe, p.s2 * (a < 2.0f ? a * a * fmaf(a, exp_tail_series<3, 17>(a), 1.0f / 6.0f) * e
+                                           : 1.0f - pe)};
+  }
+}
+
+// gamma alone (the same values as kappa_gamma_d2's .g).
+template <int KT>
+__device__ __forceinline__ float gamma_d2(const KernF& p, float d2) {
+  return kappa_gamma_d2<KT>(p, d2).g;
 }
 
 // d kappa / d lengthscale from the squared distance (FP32).
@@ -222,6 +303,8 @@ inline KernF make_kernf(const graphgp_kernel& k) {
   p.s2 = (float)k.sigma2;
   p.inv_ell = (float)(1.0 / k.lengthscale);
   p.nug = (float)k.nugget;
+  const double tol = k.rescue_tol == 0.0 ? kDefaultRescueTol : k.rescue_tol;
+  p.resc_T = tol < 0.0 ? -1.0f : (float)(tol * 16777216.0);
   p.s2d = k.sigma2;
   p.elld = k.lengthscale;
   p.nugd = k.nugget;

@@ -19,11 +19,29 @@
 namespace ggp {
 namespace {
 
+// Rows whose FP32 factor needs the FP64 rescue (rescue.cuh) are listed here
+// and recomputed afterwards by factor_rescue_kernel, one thread per row, so
+// that a warp does not stall on the FP64 row of one of its points.  A row
+// that finds the list full is recomputed in place.
+struct RescueList {
+  int64_t* rows;
+  unsigned long long* count;
+  unsigned long long cap;
+  __device__ __forceinline__ bool defer(int64_t i) const {
+    const unsigned long long slot = atomicAdd(count, 1ull);
+    if (slot < cap) {
+      rows[slot] = i;
+      return true;
+    }
+    return false;
+  }
+};
+
 template <int G, int KT>
 __global__ void __launch_bounds__(128) point_factor_kernel(
     const float4* __restrict__ xs, const int32_t* __restrict__ nbr, int64_t N, int k, int kp,
     int64_t n0, KernF kf, float* __restrict__ b_out, float* __restrict__ sigma_out,
-    double* __restrict__ logdet, unsigned long long* __restrict__ not_pd) {
+    double* __restrict__ logdet, unsigned long long* __restrict__ not_pd, RescueList rl) {
   constexpr int PPW = 32 / G;  // points per warp
   constexpr int GS = PFLayout<G>::GS;
   __shared__ __align__(16) float Ls[4 * PPW * GS];
@@ -49,9 +67,12 @@ __global__ void __launch_bounds__(128) point_factor_kernel(
     // rescue decision, uniform over the group's lanes
     const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (grp * G));
     const bool lane_bad = a < k && !isfinite(st.b_own);
-    const bool rescue = st.clamped || !(st.min_piv >= kRescuePivot * (kf.s2 + kf.nug)) ||
+    const bool rescue = st.clamped || row_error_too_large(st.max_ratio, st.varw, st.sigma, kf) ||
                         !isfinite(st.sigma) || (__ballot_sync(0xffffffffu, lane_bad) & gmask);
-    if (valid) {
+    bool deferred = false;
+    if (valid && rescue && a == 0) deferred = rl.defer(i);
+    deferred = __shfl_sync(0xffffffffu, deferred, grp * G);
+    if (valid && !deferred) {
       if (rescue) {
         if (a == 0) {
           Row64<G> R;
@@ -86,7 +107,7 @@ template <int K, int KT>
 __global__ void __launch_bounds__(128) point_factor_thread_kernel(
     const float4* __restrict__ xs, const int32_t* __restrict__ nbr, int64_t N, int k, int64_t n0,
     KernF kf, float* __restrict__ b_out, float* __restrict__ sigma_out,
-    double* __restrict__ logdet, unsigned long long* __restrict__ not_pd) {
+    double* __restrict__ logdet, unsigned long long* __restrict__ not_pd, RescueList rl) {
   LogAcc acc;
   unsigned long long clamped_rows = 0;
   const int64_t npts = N - n0;
@@ -106,7 +127,10 @@ __global__ void __launch_bounds__(128) point_factor_thread_kernel(
     PointRegs<K> p;
     const float4 xq = __ldg(xs + i);
     point_factor_thread<K, KT>(p, k, kf, x, xq);
-    if (needs_rescue(p, k, kf)) rescue_thread<K, KT>(p, xs, nbr + t * K, k, xq, kf);
+    if (needs_rescue(p, k, kf)) {
+      if (rl.defer(i)) continue;
+      rescue_thread<K, KT>(p, xs, nbr + t * K, k, xq, kf);
+    }
     float4* bo = reinterpret_cast<float4*>(b_out + t * K);
 #pragma unroll
     for (int q = 0; q < K / 4; q++)
@@ -126,7 +150,7 @@ template <int KT>
 __global__ void __launch_bounds__(128) point_factor_wide_kernel(
     const float4* __restrict__ xs, const int32_t* __restrict__ nbr, int64_t N, int k, int kp,
     int64_t n0, KernF kf, float* __restrict__ b_out, float* __restrict__ sigma_out,
-    double* __restrict__ logdet, unsigned long long* __restrict__ not_pd) {
+    double* __restrict__ logdet, unsigned long long* __restrict__ not_pd, RescueList rl) {
   extern __shared__ __align__(16) unsigned char wide_smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   WideWarp& W = reinterpret_cast<WideWarp*>(wide_smem)[warp];
@@ -142,6 +166,9 @@ __global__ void __launch_bounds__(128) point_factor_wide_kernel(
     const float4 xq = __ldg(xs + i);
     WideFactor r = point_factor_wide<KT>(W, k, kf, xq);
     if (wide_needs_rescue(W, r, k, kf)) {
+      bool deferred = false;
+      if (lane == 0) deferred = rl.defer(i);
+      if (__shfl_sync(0xffffffffu, deferred, 0)) continue;
       if (lane == 0) {
         Row64<kWideK> R;
         row_factor64<kWideK, KT>(R, xs, row, k, xq, kf);
@@ -167,6 +194,59 @@ __global__ void __launch_bounds__(128) point_factor_wide_kernel(
   if (lane == 0 && clamped_rows) atomicAdd(not_pd, clamped_rows);
 }
 
+// The FP64 rows listed by the factor kernels: b (row stride kp), sigma, and
+// their log-determinant and floor counts.
+template <int KMAX, int KT>
+__global__ void __launch_bounds__(128) factor_rescue_kernel(
+    const float4* __restrict__ xs, const int32_t* __restrict__ nbr, int k, int kp, int64_t n0,
+    KernF kf, RescueList rl, float* __restrict__ b_out, float* __restrict__ sigma_out,
+    double* __restrict__ logdet, unsigned long long* __restrict__ not_pd) {
+  LogAcc acc;
+  unsigned long long clamped_rows = 0;
+  const unsigned long long cnt = *rl.count;
+  const int64_t n = (int64_t)(cnt < rl.cap ? cnt : rl.cap);
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = rl.rows[r];
+    const int64_t t = i - n0;
+    Row64<KMAX> R;
+    row_factor64<KMAX, KT>(R, xs, nbr + t * kp, k, __ldg(xs + i), kf);
+    for (int e = 0; e < kp; e++) b_out[t * kp + e] = e < k ? (float)R.b[e] : 0.0f;
+    const float sg = (float)R.sigma;
+    sigma_out[i] = sg;
+    acc.mul(sg);
+    if (R.clamped) clamped_rows++;
+  }
+  block_add_double(acc.log_value(), logdet);
+  for (int o = 16; o; o >>= 1) clamped_rows += __shfl_xor_sync(0xffffffffu, clamped_rows, o);
+  if ((threadIdx.x & 31) == 0 && clamped_rows) atomicAdd(not_pd, clamped_rows);
+}
+
+template <int KMAX>
+int launch_rescue(int type, graphgp_graph_t g, graphgp_factor_t f, const KernF& kf,
+                  const RescueList& rl, cudaStream_t s) {
+  const unsigned grid = 4 * (unsigned)num_sms();
+#define GGP_RS(KT)                                                                          \
+  factor_rescue_kernel<KMAX, KT><<<grid, 128, 0, s>>>(g->xs, g->nbr, g->k, g->kp, g->n0, kf, \
+                                                      rl, f->b, f->sigma, f->logdet, f->not_pd)
+  switch (type) {
+    case GRAPHGP_MATERN12: GGP_RS(GRAPHGP_MATERN12); break;
+    case GRAPHGP_MATERN32: GGP_RS(GRAPHGP_MATERN32); break;
+    case GRAPHGP_MATERN52: GGP_RS(GRAPHGP_MATERN52); break;
+    default: GGP_RS(GRAPHGP_SQEXP); break;
+  }
+#undef GGP_RS
+  GGP_CUDA(cudaGetLastError());
+  return GRAPHGP_OK;
+}
+
+// What the FP32 dense factor leaves for dense_finish_kernel.
+struct DenseCheck {
+  double logdet;           // sum log L0_ii^2 of the FP32 block
+  unsigned long long bad;  // floored pivots
+  float min_piv;           // smallest pivot before flooring
+};
+
 // Dense block: K_00 (lower triangle) in global memory.
 template <int KT>
 __global__ void dense_fill_kernel(const float4* __restrict__ xs, int n0, KernF kf,
@@ -187,12 +267,15 @@ __global__ void dense_fill_kernel(const float4* __restrict__ xs, int n0, KernF k
 __global__ void __launch_bounds__(1024) dense_chol_kernel(float* __restrict__ A,
                                                           float* __restrict__ W, int n0,
                                                           float* __restrict__ sigma,
-                                                          double* __restrict__ logdet,
-                                                          unsigned long long* __restrict__ not_pd) {
+                                                          DenseCheck* __restrict__ chk) {
   extern __shared__ float rowj[];  // [n0]
   __shared__ float s_inv;
   __shared__ unsigned long long s_bad;
-  if (threadIdx.x == 0) s_bad = 0;
+  __shared__ float s_minpiv;
+  if (threadIdx.x == 0) {
+    s_bad = 0;
+    s_minpiv = A[0];
+  }
   const float k0 = A[0];
   for (int j = 0; j < n0; j++) {
     for (int m = threadIdx.x; m < j; m += blockDim.x) rowj[m] = A[(int64_t)j * n0 + m];
@@ -209,6 +292,7 @@ __global__ void __launch_bounds__(1024) dense_chol_kernel(float* __restrict__ A,
       float tv = t0 + t1;
       if (r == j) {
         float fl = kPdFloor * k0;
+        s_minpiv = fminf(s_minpiv, tv);
         if (!(tv > fl)) {
           tv = fl;
           s_bad++;
@@ -244,8 +328,11 @@ __global__ void __launch_bounds__(1024) dense_chol_kernel(float* __restrict__ A,
     sigma[i] = l;
     lsum += log((double)l * (double)l);
   }
-  block_add_double(lsum, logdet);
-  if (threadIdx.x == 0 && s_bad) atomicAdd(not_pd, s_bad);
+  block_add_double(lsum, &chk->logdet);
+  if (threadIdx.x == 0) {
+    chk->bad = s_bad;
+    chk->min_piv = s_minpiv;
+  }
 }
 
 // Dense block with the lower triangle held in shared memory (n0 <= 320): one
@@ -263,13 +350,16 @@ __device__ __forceinline__ int tri_ix(int r, int c) { return r * (r + 1) / 2 + c
 __global__ void __launch_bounds__(1024) dense_chol_smem_kernel(float* __restrict__ A,
                                                                float* __restrict__ W, int n0,
                                                                float* __restrict__ sigma,
-                                                               double* __restrict__ logdet,
-                                                               unsigned long long* __restrict__ not_pd) {
+                                                               DenseCheck* __restrict__ chk) {
   extern __shared__ float S[];         // [tri(n0)] packed lower triangle
   float* tr = S + n0 * (n0 + 1) / 2;   // [n0] column values of one step
   __shared__ unsigned long long s_bad;
+  __shared__ float s_minpiv;
   const int w = threadIdx.x >> 2, part = threadIdx.x & 3;
-  if (threadIdx.x == 0) s_bad = 0;
+  if (threadIdx.x == 0) {
+    s_bad = 0;
+    s_minpiv = A[0];
+  }
   for (int e = threadIdx.x; e < n0 * n0; e += blockDim.x) {
     const int r = e / n0, c = e - r * n0;
     if (c <= r) S[tri_ix(r, c)] = A[e];
@@ -298,6 +388,7 @@ __global__ void __launch_bounds__(1024) dense_chol_smem_kernel(float* __restrict
     for (int r = j + 1 + threadIdx.x; r < n0; r += blockDim.x) S[tri_ix(r, j)] = tr[r] * inv;
     if (threadIdx.x == 0) {
       S[tri_ix(j, j)] = ljj;
+      s_minpiv = fminf(s_minpiv, tr[j]);
       if (bad) s_bad++;
     }
     __syncthreads();
@@ -335,20 +426,103 @@ __global__ void __launch_bounds__(1024) dense_chol_smem_kernel(float* __restrict
     const int r = e / n0, c = e - r * n0;
     W[e] = c <= r ? S[tri_ix(r, c)] : 0.0f;
   }
+  block_add_double(lsum, &chk->logdet);
+  if (threadIdx.x == 0) {
+    chk->bad = s_bad;
+    chk->min_piv = s_minpiv;
+  }
+}
+
+// Accepts the FP32 dense block or recomputes it in FP64.  The FP32 block's
+// error is estimated like a conditional's (rescue.cuh): every dense row is a
+// conditional on all earlier dense points, with K_jj = K_00 for every j, so
+// est = 2^-24 (K_00 / p_min)^2 from the smallest FP32 pivot p_min.  When the
+// estimate exceeds the kernel's rescue_tol or a pivot was floored, the block
+// is refactored from the coordinates in FP64 (K_00 from FP64 distances,
+// left-looking Cholesky with the same floor, inverse by forward substitution)
+// and rounded to FP32; else the FP32 block's log-determinant and floor count
+// are taken.  One block of 1024 threads; Lw, Ww are n0 x n0 FP64 work arrays.
+template <int KT>
+__global__ void __launch_bounds__(1024) dense_finish_kernel(
+    const float4* __restrict__ xs, int n0, KernF kf, const DenseCheck* __restrict__ chk,
+    double* __restrict__ Lw, double* __restrict__ Ww, float* __restrict__ L0,
+    float* __restrict__ L0inv, float* __restrict__ sigma, double* __restrict__ logdet,
+    unsigned long long* __restrict__ not_pd) {
+  extern __shared__ double tcol[];  // [n0]
+  __shared__ unsigned long long s_bad;
+  const float k0f = kf.s2 + kf.nug;
+  const float r32 = k0f / chk->min_piv;
+  const bool redo = chk->bad > 0 || !(r32 * r32 <= kf.resc_T);
+  if (!redo) {
+    if (threadIdx.x == 0) {
+      atomicAdd(logdet, chk->logdet);
+      if (chk->bad) atomicAdd(not_pd, chk->bad);
+    }
+    return;
+  }
+  if (threadIdx.x == 0) s_bad = 0;
+  const double k0 = kf.s2d + kf.nugd;
+  for (int64_t e = threadIdx.x; e < (int64_t)n0 * n0; e += blockDim.x) {
+    const int i = (int)(e / n0), j = (int)(e % n0);
+    Lw[e] = j < i ? kappa64<KT>(kf, dist64(xs[i], xs[j])) : (j == i ? k0 : 0.0);
+  }
+  __syncthreads();
+  const double fl = kPdFloor64 * k0;
+  for (int j = 0; j < n0; j++) {
+    const double* Lj = Lw + (int64_t)j * n0;
+    for (int r = j + threadIdx.x; r < n0; r += blockDim.x) {
+      const double* Lr = Lw + (int64_t)r * n0;
+      double t = Lr[j];
+      for (int m = 0; m < j; m++) t -= Lr[m] * Lj[m];
+      tcol[r] = t;
+    }
+    __syncthreads();
+    double piv = tcol[j];
+    if (!(piv > fl)) piv = fl;
+    const double ljj = sqrt(piv);
+    for (int r = j + 1 + threadIdx.x; r < n0; r += blockDim.x) Lw[(int64_t)r * n0 + j] = tcol[r] / ljj;
+    if (threadIdx.x == 0) {
+      Lw[(int64_t)j * n0 + j] = ljj;
+      if (!(tcol[j] > fl)) s_bad++;
+    }
+    __syncthreads();
+  }
+  // L^-1 column by column (forward substitution), one column per thread
+  for (int c = threadIdx.x; c < n0; c += blockDim.x) {
+    Ww[(int64_t)c * n0 + c] = 1.0 / Lw[(int64_t)c * n0 + c];
+    for (int i = c + 1; i < n0; i++) {
+      const double* Li = Lw + (int64_t)i * n0;
+      double t = 0.0;
+      for (int m = c; m < i; m++) t += Li[m] * Ww[(int64_t)m * n0 + c];
+      Ww[(int64_t)i * n0 + c] = -t / Li[i];
+    }
+  }
+  __syncthreads();
+  double lsum = 0.0;
+  for (int64_t e = threadIdx.x; e < (int64_t)n0 * n0; e += blockDim.x) {
+    const int i = (int)(e / n0), j = (int)(e % n0);
+    L0[e] = j <= i ? (float)Lw[e] : 0.0f;
+    L0inv[e] = j <= i ? (float)Ww[e] : 0.0f;
+    if (i == j) {
+      const float l = (float)Lw[e];
+      sigma[i] = l;
+      lsum += log((double)l * (double)l);
+    }
+  }
   block_add_double(lsum, logdet);
   if (threadIdx.x == 0 && s_bad) atomicAdd(not_pd, s_bad);
 }
 
 template <int G>
 int launch_point(int type, graphgp_graph_t g, graphgp_factor_t f, const KernF& kf,
-                 cudaStream_t s) {
+                 const RescueList& rl, cudaStream_t s) {
   int64_t npts = g->N - g->n0;
   constexpr int PPW = 32 / G;
   int64_t groups_per_block = 4 * PPW;
   unsigned grid = grid_for((npts + groups_per_block - 1) / groups_per_block * 128, 128, 16);
 #define GGP_PF(KT)                                                                       \
   point_factor_kernel<G, KT><<<grid, 128, 0, s>>>(g->xs, g->nbr, g->N, g->k, g->kp, g->n0, \
-                                                  kf, f->b, f->sigma, f->logdet, f->not_pd)
+                                                  kf, f->b, f->sigma, f->logdet, f->not_pd, rl)
   switch (type) {
     case GRAPHGP_MATERN12: GGP_PF(GRAPHGP_MATERN12); break;
     case GRAPHGP_MATERN32: GGP_PF(GRAPHGP_MATERN32); break;
@@ -362,12 +536,12 @@ int launch_point(int type, graphgp_graph_t g, graphgp_factor_t f, const KernF& k
 
 template <int K>
 int launch_point_thread(int type, graphgp_graph_t g, graphgp_factor_t f, const KernF& kf,
-                        cudaStream_t s) {
+                        const RescueList& rl, cudaStream_t s) {
   const int64_t npts = g->N - g->n0;
   const unsigned grid = grid_for(npts, 128, 8);
 #define GGP_PT(KT)                                                                       \
   point_factor_thread_kernel<K, KT><<<grid, 128, 0, s>>>(g->xs, g->nbr, g->N, g->k, g->n0, kf, \
-                                                         f->b, f->sigma, f->logdet, f->not_pd)
+                                                         f->b, f->sigma, f->logdet, f->not_pd, rl)
   switch (type) {
     case GRAPHGP_MATERN12: GGP_PT(GRAPHGP_MATERN12); break;
     case GRAPHGP_MATERN32: GGP_PT(GRAPHGP_MATERN32); break;
@@ -380,9 +554,10 @@ int launch_point_thread(int type, graphgp_graph_t g, graphgp_factor_t f, const K
 }
 
 constexpr int kWideWarps = 4;  // warps per block of the wide kernels
+constexpr int64_t kRescueListMax = 1 << 20;  // rows listed for the FP64 rescue kernel
 
 int launch_point_wide(int type, graphgp_graph_t g, graphgp_factor_t f, const KernF& kf,
-                      cudaStream_t s) {
+                      const RescueList& rl, cudaStream_t s) {
   const int64_t npts = g->N - g->n0;
   const size_t smem = kWideWarps * sizeof(WideWarp);
   const unsigned grid = grid_for((npts + kWideWarps - 1) / kWideWarps * 128, 128, 4);
@@ -390,7 +565,7 @@ int launch_point_wide(int type, graphgp_graph_t g, graphgp_factor_t f, const Ker
   GGP_CUDA(cudaFuncSetAttribute(point_factor_wide_kernel<KT>,                                \
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));    \
   point_factor_wide_kernel<KT><<<grid, 32 * kWideWarps, smem, s>>>(                          \
-      g->xs, g->nbr, g->N, g->k, g->kp, g->n0, kf, f->b, f->sigma, f->logdet, f->not_pd)
+      g->xs, g->nbr, g->N, g->k, g->kp, g->n0, kf, f->b, f->sigma, f->logdet, f->not_pd, rl)
   switch (type) {
     case GRAPHGP_MATERN12: GGP_PW(GRAPHGP_MATERN12); break;
     case GRAPHGP_MATERN32: GGP_PW(GRAPHGP_MATERN32); break;
@@ -407,16 +582,23 @@ int launch_point_wide(int type, graphgp_graph_t g, graphgp_factor_t f, const Ker
 int point_factor(graphgp_graph_t g, graphgp_factor_t f, const KernF& kf, int type,
                  cudaStream_t s) {
   if (g->N <= g->n0) return GRAPHGP_OK;
+  const int64_t npts = g->N - g->n0;
+  Scratch sc(s);
+  RescueList rl;
+  rl.cap = (unsigned long long)std::min<int64_t>(npts, kRescueListMax);
+  GGP_TRY(sc.alloc(&rl.rows, rl.cap));
+  GGP_TRY(sc.alloc(&rl.count, 1));
+  GGP_CUDA(cudaMemsetAsync(rl.count, 0, sizeof(unsigned long long), s));
   switch (g->kp) {
-    case 4: return launch_point_thread<4>(type, g, f, kf, s);
-    case 8: return launch_point_thread<8>(type, g, f, kf, s);
-    case 12: return launch_point_thread<12>(type, g, f, kf, s);
-    case 16: return launch_point_thread<16>(type, g, f, kf, s);
+    case 4: GGP_TRY(launch_point_thread<4>(type, g, f, kf, rl, s)); return launch_rescue<4>(type, g, f, kf, rl, s);
+    case 8: GGP_TRY(launch_point_thread<8>(type, g, f, kf, rl, s)); return launch_rescue<8>(type, g, f, kf, rl, s);
+    case 12: GGP_TRY(launch_point_thread<12>(type, g, f, kf, rl, s)); return launch_rescue<12>(type, g, f, kf, rl, s);
+    case 16: GGP_TRY(launch_point_thread<16>(type, g, f, kf, rl, s)); return launch_rescue<16>(type, g, f, kf, rl, s);
     case 20:
     case 24:
     case 28:
-    case 32: return launch_point<32>(type, g, f, kf, s);
-    default: return launch_point_wide(type, g, f, kf, s);
+    case 32: GGP_TRY(launch_point<32>(type, g, f, kf, rl, s)); return launch_rescue<32>(type, g, f, kf, rl, s);
+    default: GGP_TRY(launch_point_wide(type, g, f, kf, rl, s)); return launch_rescue<kWideK>(type, g, f, kf, rl, s);
   }
 }
 
@@ -431,16 +613,34 @@ int dense_factor(graphgp_graph_t g, graphgp_factor_t f, const KernF& kf, int typ
     default: dense_fill_kernel<GRAPHGP_SQEXP><<<grid, 256, 0, s>>>(g->xs, n0, kf, f->L0); break;
   }
   GGP_CUDA(cudaGetLastError());
+  Scratch sc(s);
+  DenseCheck* chk = nullptr;
+  double* work = nullptr;
+  GGP_TRY(sc.alloc(&chk, 1));
+  GGP_TRY(sc.alloc(&work, 2 * (size_t)n0 * n0));
+  GGP_CUDA(cudaMemsetAsync(chk, 0, sizeof(DenseCheck), s));
   if (n0 <= kDenseSmemMax) {
     const size_t smem = ((size_t)n0 * (n0 + 1) / 2 + n0) * sizeof(float);
     GGP_CUDA(cudaFuncSetAttribute(dense_chol_smem_kernel,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    dense_chol_smem_kernel<<<1, 1024, smem, s>>>(f->L0, f->L0inv, n0, f->sigma, f->logdet,
-                                                 f->not_pd);
+    dense_chol_smem_kernel<<<1, 1024, smem, s>>>(f->L0, f->L0inv, n0, f->sigma, chk);
   } else {
-    dense_chol_kernel<<<1, 1024, n0 * sizeof(float), s>>>(f->L0, f->L0inv, n0, f->sigma,
-                                                          f->logdet, f->not_pd);
+    dense_chol_kernel<<<1, 1024, n0 * sizeof(float), s>>>(f->L0, f->L0inv, n0, f->sigma, chk);
   }
+  GGP_CUDA(cudaGetLastError());
+  double* Lw = work;
+  double* Ww = work + (size_t)n0 * n0;
+  const size_t smem64 = (size_t)n0 * sizeof(double);
+#define GGP_DF(KT)                                                                             \
+  dense_finish_kernel<KT><<<1, 1024, smem64, s>>>(g->xs, n0, kf, chk, Lw, Ww, f->L0, f->L0inv, \
+                                                  f->sigma, f->logdet, f->not_pd)
+  switch (type) {
+    case GRAPHGP_MATERN12: GGP_DF(GRAPHGP_MATERN12); break;
+    case GRAPHGP_MATERN32: GGP_DF(GRAPHGP_MATERN32); break;
+    case GRAPHGP_MATERN52: GGP_DF(GRAPHGP_MATERN52); break;
+    default: GGP_DF(GRAPHGP_SQEXP); break;
+  }
+#undef GGP_DF
   GGP_CUDA(cudaGetLastError());
   return GRAPHGP_OK;
 }
@@ -454,7 +654,7 @@ extern "C" int graphgp_factor(graphgp_graph_t g, const graphgp_kernel* kern, voi
   if (!out) return GRAPHGP_ERR_INVALID;
   *out = nullptr;
   if (!g || !kern || kern->type < 0 || kern->type > 3 || !(kern->sigma2 > 0) ||
-      !(kern->lengthscale > 0) || !(kern->nugget >= 0))
+      !(kern->lengthscale > 0) || !(kern->nugget >= 0) || !std::isfinite(kern->rescue_tol))
     return GRAPHGP_ERR_INVALID;
   cudaStream_t s = (cudaStream_t)stream;
   graphgp_factor_t f = new (std::nothrow) graphgp_factor_s();

@@ -152,7 +152,7 @@ __global__ void nll_fused_finish_kernel(const double* __restrict__ sq,
 
 bool valid_kernel(const graphgp_kernel* kern) {
   return kern && kern->type >= 0 && kern->type <= 3 && kern->sigma2 > 0 &&
-         kern->lengthscale > 0 && kern->nugget >= 0;
+         kern->lengthscale > 0 && kern->nugget >= 0 && std::isfinite(kern->rescue_tol);
 }
 
 // Dense block of the fused forms into a temporary handle whose arrays live in

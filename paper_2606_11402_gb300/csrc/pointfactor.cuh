@@ -1,16 +1,46 @@
-// Per-point conditional factor of Sec. 2.1 Eq. 2, computed by a group of G
-// lanes of one warp (G = 8, 16 or 32 >= k).  Shared by the factor kernel and
-// the adjoint kernels, which recompute the factors instead of storing them,
-// so that both see bit-identical b and sigma.
+// Per-point conditional factor of Sec. 2.1 Eq. 2 in FP32: the weights
+// b_i = K_ic K_cc^-1 and sigma_i^2 = K_ii - K_ic K_cc^-1 K_ci.
 //
-// Lane a holds row a of K_cc in registers.  Left-looking Cholesky: at step j
-// every lane forms its Schur value t_a = K_aj - sum_{m<j} L_am L_jm from its
-// own row and row j of L (published in shared memory by lane j at earlier
-// steps); lane j's t is the pivot.  The forward solve y = L^-1 K_ci rides
-// along, sigma^2 = K_ii - y.y accumulates in compensated FP32 (exact
-// two-product, two-sum), and b = L^-T y is a backward sweep over L's columns.
-// Rows and columns k..G-1 are identity padding.  A pivot at or below 1e-7 of
-// its diagonal entry is raised to that floor and flagged.
+// Increment form.  Where neighbours are close on the scale of the
+// lengthscale, every entry of K_cc is close to kappa(0): FP32 keeps only the
+// leading digits of kappa(r), and the Cholesky of K_cc then cancels them
+// (condition numbers of 1e5-1e11 on the measured clouds).  Such rows are
+// factored in increments of the field instead, an exact change of variables:
+// with c_0 the nearest neighbour, z_0 = x(c_0), z_a = x(c_a) - x(c_0)
+// (a >= 1) and the target w = x(i) - x(c_0),
+//   M_00 = kappa(0) + nugget,       M_a0 = -(g_a0 + nugget),
+//   M_ab = (g_a0 + g_b0) - g_ab + nugget (1 + [a = b]),
+//   m_0  = -(g_0i + nugget),        m_a  = (g_a0 + g_0i) - g_ai + nugget,
+//   Var(w) = 2 (g_0i + nugget),
+// where g = kappa(0) - kappa(r) is the variogram, evaluated with a small
+// relative error even as r -> 0 (gamma_d2).  With L = chol(M),
+// y = L^-1 m and beta = L^-T y, E[w | z] = beta . z gives the weights
+// b_a = beta_a (a >= 1), b_0 = 1 + beta_0 - sum_{a>=1} beta_a, and
+// sigma^2 = Var(w) - y.y.  The change of variables is unit lower triangular,
+// so the pivots of M equal those of K_cc (conditional variances) and the
+// floor policy below is the covariance form's; only the rounding differs.
+// K_cc^-1 r (the backward) is T^T M^-1 T r with (T r)_a = r_a - r_0.
+// A row whose nearest neighbour is far (g_0i >= kappa(0) / 2) has small
+// weights, which the recovery of b_0 would swamp with its rounding error; it
+// keeps the covariance form (M = K_cc, m = K_ci, Var(w) = K_ii, b = beta,
+// T = identity).  The choice is made per row from g_0i.
+//
+// A pivot at or below 1e-7 of kappa(0) + nugget is raised to that floor and
+// flagged; so is sigma^2.  max_ratio = max_j M_jj / pivot_j (pivot after the
+// floor) bounds the scaled
+// condition number of M from below; with Var(w) / sigma^2 (the cancellation
+// in sigma^2) it forms the row's error estimate (rescue.cuh).
+//
+// Group form: a group of G lanes of one warp (G = 8, 16 or 32 >= k), lane a
+// holding row a of M in registers.  Left-looking Cholesky: at step j every
+// lane forms its Schur value t_a = M_aj - sum_{m<j} L_am L_jm from its own
+// row and row j of L (published in shared memory by lane j at earlier
+// steps); lane j's t is the pivot.  The forward solve y = L^-1 m rides along,
+// sigma^2 = Var(w) - y.y accumulates in compensated FP32 (exact two-product,
+// two-sum), and beta = L^-T y is a backward sweep over L's columns.  Rows and
+// columns k..G-1 are identity padding.  Shared by the factor kernel and the
+// adjoint kernels, which recompute the factors instead of storing them, so
+// that both see bit-identical b and sigma.
 #pragma once
 
 #include <type_traits>
@@ -68,15 +98,17 @@ __device__ __forceinline__ DF df_sub_square(DF s, float y) {
 
 template <int G>
 struct PointState {
-  float A[G];      // row a of L (lower part valid)
+  float A[G];      // row a of M, then of L (lower part valid)
   float D2[G];     // squared distances |x_a - x_b|^2 of row a
   float d2q;       // |x_a - x_i|^2
   float inv_own;   // 1 / L_aa
   float y_own;     // y_a
-  float b_own;     // b_a
+  float b_own;     // b_a (covariance-form weight of neighbour a)
   float sigma;     // conditional standard deviation (same on all lanes)
   bool clamped;    // a pivot was floored (same on all lanes)
-  float min_piv;   // smallest pivot before flooring (same on all lanes)
+  float max_ratio; // max_j M_jj / pivot_j before flooring (same on all lanes)
+  float varw;      // Var(w) (same on all lanes)
+  bool inc;        // increment form (same on all lanes)
 };
 
 // Shared-memory row stride and per-group footprint (floats) for G lanes.
@@ -94,6 +126,14 @@ __device__ __forceinline__ void point_factor_group(PointState<G>& st, int a, int
   const unsigned full = 0xffffffffu;
   const bool real = a < k;
   const float k0 = kf.s2 + kf.nug;
+  const float nug = kf.nug;
+  st.d2q = sqdist(xa, xq);
+  const KG qa = kappa_gamma_d2<KT>(kf, st.d2q);
+  st.inc = __shfl_sync(full, qa.g, 0, G) < 0.5f * kf.s2;
+  const bool inc = st.inc;
+  const float eai = inc ? qa.g : qa.k;  // entry (a, i) before the change of variables
+  const float e0i = __shfl_sync(full, eai, 0, G);
+  float ea0 = 0.0f;  // entry (a, 0)
 #pragma unroll
   for (int bcol = 0; bcol < G; bcol++) {
     float bx = __shfl_sync(full, xa.x, bcol, G);
@@ -102,16 +142,32 @@ __device__ __forceinline__ void point_factor_group(PointState<G>& st, int a, int
     float dx = xa.x - bx, dy = xa.y - by, dz = xa.z - bz;
     float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
     st.D2[bcol] = d2;
-    float kv = kappa_d2<KT>(kf, d2);
-    bool both = real && bcol < k;
-    st.A[bcol] = (bcol == a) ? (real ? k0 : 1.0f) : (both ? kv : 0.0f);
+    const KG kg = kappa_gamma_d2<KT>(kf, d2);
+    const float ev = inc ? kg.g : kg.k;
+    if (bcol == 0) ea0 = ev;
+    const float e0b = __shfl_sync(full, ev, 0, G);  // entry (0, bcol) from row 0
+    const bool both = real && bcol < k;
+    float m;
+    if (bcol == a) {
+      m = real ? ((a == 0 || !inc) ? k0 : 2.0f * (ea0 + nug)) : 1.0f;
+    } else if (!inc) {
+      m = ev;
+    } else if (a == 0) {
+      m = -(e0b + nug);
+    } else if (bcol == 0) {
+      m = -(ea0 + nug);
+    } else {
+      m = ((ea0 + e0b) - ev) + nug;
+    }
+    st.A[bcol] = both || bcol == a ? m : 0.0f;
   }
-  st.d2q = sqdist(xa, xq);
-  float c = real ? kappa_d2<KT>(kf, st.d2q) : 0.0f;
-  const float diag = real ? k0 : 1.0f;
-  DF s2{k0, 0.0f};
+  float c = !real ? 0.0f
+                  : !inc ? eai : (a == 0 ? -(e0i + nug) : ((ea0 + e0i) - eai) + nug);
+  st.varw = inc ? 2.0f * (e0i + nug) : k0;
+  DF s2{st.varw, 0.0f};
+  const float pfloor = kPdFloor * k0;
   st.clamped = false;
-  st.min_piv = k0;
+  st.max_ratio = 1.0f;
   st.inv_own = 1.0f;
   st.y_own = 0.0f;
 #pragma unroll
@@ -129,16 +185,16 @@ __device__ __forceinline__ void point_factor_group(PointState<G>& st, int a, int
     }
 #pragma unroll
     for (int m = (j / 4) * 4; m < j; m++) tv = fmaf(-st.A[m], Lg[j * SG + m], tv);
+    const float mjj = __shfl_sync(full, st.A[j], j, G);
     tv += t2;
     float piv = __shfl_sync(full, tv, j, G);
-    float pfloor = kPdFloor * __shfl_sync(full, diag, j, G);
-    st.min_piv = fminf(st.min_piv, piv);
     if (!(piv > pfloor)) {
       piv = pfloor;
       st.clamped = true;
     }
     float ljj = sqrtf(piv);
     float inv = 1.0f / ljj;
+    st.max_ratio = fmaxf(st.max_ratio, mjj * inv * inv);
     float laj = (a == j) ? ljj : tv * inv;
     st.A[j] = laj;
     if (a == j) st.inv_own = inv;
@@ -150,12 +206,12 @@ __device__ __forceinline__ void point_factor_group(PointState<G>& st, int a, int
     __syncwarp(full);
   }
   float sig2 = s2.hi + s2.lo;
-  if (!(sig2 > kPdFloor * k0)) {
-    sig2 = kPdFloor * k0;
+  if (!(sig2 > pfloor)) {
+    sig2 = pfloor;
     st.clamped = true;
   }
   st.sigma = sqrtf(sig2);
-  // b = L^-T y, last entry first; lane a keeps d_a = y_a - sum_{m>a} L_ma b_m
+  // beta = L^-T y, last entry first; lane a keeps d_a = y_a - sum_{m>a} L_ma beta_m
   float d = st.y_own;
   st.b_own = 0.0f;
 #pragma unroll
@@ -165,15 +221,23 @@ __device__ __forceinline__ void point_factor_group(PointState<G>& st, int a, int
     if (a == j) st.b_own = bj;
     if (a < j) d = fmaf(-Lg[j * SG + a], bj, d);
   }
+  // increment form: b_0 = 1 + beta_0 - sum_{a>=1} beta_a (summed in lane order)
+  float sb = 0.0f;
+#pragma unroll
+  for (int j = 1; j < G; j++) sb += __shfl_sync(full, st.b_own, j, G);
+  if (a == 0 && inc) st.b_own = (1.0f + st.b_own) - sb;
 }
 
 // Solves K_cc g = r for the factor held by the group (L rows in st.A and in
-// Lg); lane a supplies r_a and receives g_a.
+// Lg): g = T^T M^-1 T r.  Lane a supplies r_a (zero for a >= k) and receives
+// g_a.
 template <int G>
 __device__ __forceinline__ float group_chol_solve(const PointState<G>& st, int a, int k,
                                                   float r, const float* Lg) {
   constexpr int SG = PFLayout<G>::SG;
   const unsigned full = 0xffffffffu;
+  const float r0 = __shfl_sync(full, r, 0, G);
+  if (st.inc && a >= 1 && a < k) r -= r0;
   float z_own = 0.0f;
 #pragma unroll
   for (int j = 0; j < G; j++) {
@@ -190,6 +254,10 @@ __device__ __forceinline__ float group_chol_solve(const PointState<G>& st, int a
     if (a == j) g_own = gj;
     if (a < j) d = fmaf(-Lg[j * SG + a], gj, d);
   }
+  float sg = 0.0f;
+#pragma unroll
+  for (int j = 1; j < G; j++) sg += __shfl_sync(full, g_own, j, G);
+  if (a == 0 && st.inc) g_own -= sg;
   return g_own;
 }
 
@@ -198,8 +266,8 @@ __device__ __forceinline__ float group_chol_solve(const PointState<G>& st, int a
 // ---- one thread per point (k <= 16) ----------------------------------------
 // The same arithmetic as point_factor_group, element by element and in the
 // same order, but with the whole lower triangle of L in one thread's
-// registers: no shuffles, no shared memory, each kernel value evaluated once
-// (the group form evaluates every row in full on its lanes).  K is the padded
+// registers: no shuffles, no shared memory, each variogram value evaluated
+// once (the group form evaluates every row in full on its lanes).  K is the padded
 // row length (4, 8, 12 or 16); entries a >= k are identity padding, which
 // passes through every step without changing the real entries (unit pivot,
 // zero off-diagonal, zero right-hand side), so all loops run K steps.  The
@@ -218,11 +286,13 @@ __device__ __forceinline__ void static_for(F&& f) {
 
 template <int K>
 struct PointRegs {
-  float L[K * (K + 1) / 2];  // L[tri(a, c)], c <= a
-  float y[K];                // y = L^-1 K_ci, then b = L^-T y (zero for a >= k)
+  float L[K * (K + 1) / 2];  // M, then L = chol(M): L[tri(a, c)], c <= a
+  float y[K];                // m, y = L^-1 m, beta = L^-T y, then b (zero for a >= k)
   float sigma;
   bool clamped;
-  float min_piv;             // smallest pivot before flooring
+  float max_ratio;           // max_j M_jj / pivot_j before flooring
+  float varw;                // Var(w)
+  bool inc;                  // increment form
   // 1 / L_jj, recomputed where needed (the same correctly rounded quotient)
   __device__ __forceinline__ float inv(int j) const { return 1.0f / L[tri(j, j)]; }
 };
@@ -249,29 +319,62 @@ template <int K, int KT>
 __device__ __forceinline__ void point_factor_thread(PointRegs<K>& p, int k, const KernF& kf,
                                                     const float4 (&x)[K], float4 xq) {
   const float k0 = kf.s2 + kf.nug;
-  // last row first: coordinates x_a die as soon as row a is filled
+  const float nug = kf.nug;
+  const KG q0 = kappa_gamma_d2<KT>(kf, sqdist(x[0], xq));
+  const bool inc = q0.g < 0.5f * kf.s2;
+  p.inc = inc;
+  // gamma (increment form) or kappa (covariance form) of every pair and of
+  // every neighbour with the point, last row first: coordinates x_a die as
+  // soon as row a is filled
   static_for<0, K>([&](auto Ar) {
     constexpr int a = K - 1 - decltype(Ar)::value;
     const bool real = a < k;
 #pragma unroll
-    for (int c = 0; c < a; c++) p.L[tri(a, c)] = real ? kappa_d2<KT>(kf, sqdist(x[a], x[c])) : 0.0f;
-    p.L[tri(a, a)] = real ? k0 : 1.0f;
-    p.y[a] = real ? kappa_d2<KT>(kf, sqdist(x[a], xq)) : 0.0f;
+    for (int c = 0; c < a; c++) {
+      const KG kg = kappa_gamma_d2<KT>(kf, sqdist(x[a], x[c]));
+      p.L[tri(a, c)] = real ? (inc ? kg.g : kg.k) : 0.0f;
+    }
+    if constexpr (a == 0) {
+      p.y[0] = inc ? q0.g : q0.k;
+    } else {
+      const KG kg = kappa_gamma_d2<KT>(kf, sqdist(x[a], xq));
+      p.y[a] = real ? (inc ? kg.g : kg.k) : 0.0f;
+    }
   });
-  DF s2{k0, 0.0f};
+  // M and m (column 0 last: in the increment form its entries are g_a0)
+  const float e0i = p.y[0];
+  static_for<1, K>([&](auto Ac) {
+    constexpr int a = decltype(Ac)::value;
+    const bool real = a < k;
+    const float ea0 = p.L[tri(a, 0)];
+#pragma unroll
+    for (int c = 1; c < a; c++)
+      p.L[tri(a, c)] = real ? (inc ? ((ea0 + p.L[tri(c, 0)]) - p.L[tri(a, c)]) + nug : p.L[tri(a, c)])
+                            : 0.0f;
+    p.L[tri(a, a)] = real ? (inc ? 2.0f * (ea0 + nug) : k0) : 1.0f;
+    p.y[a] = real ? (inc ? ((ea0 + e0i) - p.y[a]) + nug : p.y[a]) : 0.0f;
+  });
+#pragma unroll
+  for (int a = 1; a < K; a++)
+    p.L[tri(a, 0)] = a < k ? (inc ? -(p.L[tri(a, 0)] + nug) : p.L[tri(a, 0)]) : 0.0f;
+  p.L[tri(0, 0)] = k0;
+  p.y[0] = inc ? -(e0i + nug) : e0i;
+  p.varw = inc ? 2.0f * (e0i + nug) : k0;
+  DF s2{p.varw, 0.0f};
   bool clamped = false;
-  float min_piv = k0;
+  float max_ratio = 1.0f;
   const float pfloor = kPdFloor * k0;
   static_for<0, K>([&](auto Jc) {
     constexpr int j = decltype(Jc)::value;
+    const float mjj = p.L[tri(j, j)];
     float piv = schur_value<K, j, j>(p);
-    min_piv = fminf(min_piv, piv);
     if (!(piv > pfloor)) {
       piv = pfloor;
       clamped = true;
     }
     const float ljj = sqrtf(piv);
     const float inv = 1.0f / ljj;
+    max_ratio = fmaxf(max_ratio, mjj * inv * inv);  // padding: 1
     static_for<j + 1, K>([&](auto Ac) {
       constexpr int a = decltype(Ac)::value;
       p.L[tri(a, j)] = schur_value<K, j, a>(p) * inv;
@@ -289,9 +392,9 @@ __device__ __forceinline__ void point_factor_thread(PointRegs<K>& p, int k, cons
     clamped = true;
   }
   p.clamped = clamped;
-  p.min_piv = min_piv;
+  p.max_ratio = max_ratio;
   p.sigma = sqrtf(sig2);
-  // b = L^-T y, last entry first
+  // beta = L^-T y, last entry first
   static_for<0, K>([&](auto Jr) {
     constexpr int j = K - 1 - decltype(Jr)::value;
     const float bj = p.y[j] * p.inv(j);
@@ -299,12 +402,21 @@ __device__ __forceinline__ void point_factor_thread(PointRegs<K>& p, int k, cons
 #pragma unroll
     for (int a = 0; a < j; a++) p.y[a] = fmaf(-p.L[tri(j, a)], bj, p.y[a]);
   });
+  // increment form: b_0 = 1 + beta_0 - sum_{a>=1} beta_a (padding entries are zero)
+  float sb = 0.0f;
+#pragma unroll
+  for (int a = 1; a < K; a++) sb += p.y[a];
+  if (inc) p.y[0] = (1.0f + p.y[0]) - sb;
 }
 
-// Solves K_cc g = r in place with the factor of point_factor_thread (same
-// operation order as group_chol_solve); r must be zero at padding entries.
+// Solves K_cc g = r in place with the factor of point_factor_thread
+// (g = T^T M^-1 T r, same operation order as group_chol_solve); r must be
+// zero at padding entries.
 template <int K>
-__device__ __forceinline__ void thread_chol_solve(const PointRegs<K>& p, float (&r)[K]) {
+__device__ __forceinline__ void thread_chol_solve(const PointRegs<K>& p, int k, float (&r)[K]) {
+#pragma unroll
+  for (int a = 1; a < K; a++)
+    if (p.inc && a < k) r[a] -= r[0];
   static_for<0, K>([&](auto Jc) {
     constexpr int j = decltype(Jc)::value;
     const float zj = r[j] * p.inv(j);
@@ -319,14 +431,19 @@ __device__ __forceinline__ void thread_chol_solve(const PointRegs<K>& p, float (
 #pragma unroll
     for (int a = 0; a < j; a++) r[a] = fmaf(-p.L[tri(j, a)], gj, r[a]);
   });
+  float sg = 0.0f;
+#pragma unroll
+  for (int a = 1; a < K; a++) sg += r[a];
+  if (p.inc) r[0] -= sg;
 }
 
 // Whether a conditional computed in FP32 must be recomputed in FP64 (see
-// rescue.cuh): a floored pivot or sigma^2, a pivot below kRescuePivot of the
-// diagonal, or a non-finite weight or sigma.
+// rescue.cuh): a floored pivot or sigma^2, a row-error estimate above the
+// kernel's threshold, or a non-finite weight or sigma.
 template <int K>
 __device__ __forceinline__ bool needs_rescue(const PointRegs<K>& p, int k, const KernF& kf) {
-  bool bad = p.clamped || !(p.min_piv >= kRescuePivot * (kf.s2 + kf.nug)) || !isfinite(p.sigma);
+  bool bad = p.clamped || row_error_too_large(p.max_ratio, p.varw, p.sigma, kf) ||
+             !isfinite(p.sigma);
 #pragma unroll
   for (int a = 0; a < K; a++) bad |= !isfinite(p.y[a]);
   return bad;

@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(128) position_backward_kernel(
     const float sbar = (alpha * xii + nllbar / sigma) / (2.0f * sigma);
     for (int a = lane; a < k; a += 32) W.g[a] = alpha * v[row[a]];
     __syncwarp();
-    wide_chol_solve(W, k);
+    wide_chol_solve(W, k, r.inc);
     double qx = 0.0, qy = 0.0, qz = 0.0;  // terms of the point itself
     for (int a = lane; a < k; a += 32) {
       const float ga = W.g[a], ba = W.y[a];

@@ -1,26 +1,38 @@
 // FP64 rescue of single conditionals (Sec. 2.1 Eq. 2).
 //
-// The per-point factors run in FP32.  Their error grows like cond(K_cc) 2^-24,
-// and when neighbours nearly coincide on the scale of the lengthscale (the
-// large-dynamic-range cloud without nugget has cond(K_cc) up to 1e11) the
-// FP32 Cholesky keeps positive pivots but its backward solve overflows: b is
-// no longer finite.  A row whose FP32 factor floored a pivot or sigma^2, whose
-// smallest pivot fell below kRescuePivot of the diagonal, or whose b or sigma
-// is not finite is recomputed here in FP64 from the FP32 coordinates: kernel
+// The per-point factors run in FP32 in the increment form of pointfactor.cuh.
+// Their error grows like the scaled condition number of the increment
+// covariance M times 2^-24, and sigma^2 = Var(w) - y.y, which cancels, loses
+// another factor Var(w) / sigma^2.  Both factors come out of the FP32
+// Cholesky: max_j M_jj / pivot_j bounds the scaled condition number from
+// below, so
+//   est = 2^-24 max_j (M_jj / pivot_j) Var(w) / sigma^2
+// is an a-priori estimate of the row's relative error.  A row whose estimate
+// exceeds the kernel's rescue_tol (graphgp.h), whose FP32 factor floored a
+// pivot or sigma^2, or whose b or sigma is not finite is recomputed here in
+// FP64 from the FP32 coordinates, in the covariance form of Eq. 2: kernel
 // values from FP64 distances, Cholesky by rows, forward and backward solves,
 // sigma^2 = K_ii - y.y, with the same pivot floor (1e-7 of the diagonal).
 // Every kernel that evaluates a conditional (factor, on-the-fly sweeps,
 // factor backward) takes the same decision on the same FP32 values and calls
-// the same code, so stored and recomputed factors agree.  On the measured
-// workloads with a nugget no row needs it.
+// the same code, so stored and recomputed factors agree.
 #pragma once
 
 #include "common.cuh"
 
 namespace ggp {
 
-constexpr float kRescuePivot = 1e-6f;
 constexpr double kPdFloor64 = 1e-7;
+
+// The row-error estimate above against the kernel's threshold (kf.resc_T =
+// rescue_tol 2^24, negative = every row): true when the FP32 row must be
+// recomputed.  A non-positive pivot makes the ratio negative or infinite;
+// such rows were floored and are rescued by the caller's clamp test anyway.
+__device__ __forceinline__ bool row_error_too_large(float max_ratio, float varw, float sigma,
+                                                    const KernF& kf) {
+  const float est = max_ratio * (varw / (sigma * sigma));
+  return !(est <= kf.resc_T);
+}
 
 __host__ __device__ constexpr int tri64(int a, int c) { return a * (a + 1) / 2 + c; }
 

@@ -38,3 +38,13 @@ extern "C" int graphgp_selftest_wait_timeout(int64_t max_spin, void* stream) {
   if (h[2] != 0) return GRAPHGP_ERR_INVALID;  // a wait passed without arrivals
   return (h[1] & ERRBIT_TIMEOUT) ? GRAPHGP_ERR_TIMEOUT : GRAPHGP_OK;
 }
+
+// Target of the device code actually loaded: binaryVersion of one of the
+// library's kernels (major * 10 + minor, 103 for sm_103a).
+extern "C" int graphgp_binary_version(int* version) {
+  if (!version) return GRAPHGP_ERR_INVALID;
+  cudaFuncAttributes a;
+  GGP_CUDA(cudaFuncGetAttributes(&a, (const void*)barrier_timeout_kernel));
+  *version = a.binaryVersion;
+  return GRAPHGP_OK;
+}

@@ -141,3 +141,8 @@ def test_graph_import_of_oracle_graph(gpu_lib):
     bad[10, 0] = want["level_offsets"][-1] - 1  # a neighbour in a later level
     with pytest.raises(gpu_lib.GraphGPError):
         gpu_lib.graph_import(pts, 8, want["n0"], want["order"], bad, want["level_offsets"])
+
+
+def test_kernels_report_sm103(gpu_lib):
+    """The device code the library loaded was compiled for sm_103a (GB300)."""
+    assert gpu_lib.binary_version() == 103
