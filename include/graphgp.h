@@ -78,7 +78,7 @@ typedef struct {
                          bounds cond(K_cc) from below, K_00 / sigma^2 is the
                          cancellation in sigma^2 = K_ii - K_ic b).  A row with
                          est > rescue_tol, a floored pivot or a non-finite
-                         result is recomputed in FP64.  0 = default 2^-6;
+                         result is recomputed in FP64.  0 = default 2^-10;
                          < 0 = every conditional in FP64 (slow on GB300:
                          FP64 runs at 1/64 of the FP32 rate).  Must be
                          finite. */

@@ -177,8 +177,8 @@ struct KernF {
 };
 
 // Default per-row error estimate above which a conditional is recomputed in
-// FP64 (rescue.cuh): 2^-6.
-constexpr double kDefaultRescueTol = 0.015625;
+// FP64 (rescue.cuh): 2^-10, about 1e-3.
+constexpr double kDefaultRescueTol = 0.0009765625;
 
 template <int KT>
 __device__ __forceinline__ float kappa_d2(const KernF& p, float d2) {

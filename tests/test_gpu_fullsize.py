@@ -18,7 +18,7 @@ import torch
 import oracle
 import workloads
 from fullsize import check_depth_and_order, check_tree, inorder_rank_of, inorder_ranks, knn_sample
-from gpu_util import fp32_tolerance, gpu_graph_arrays, np_, rel_norm, row_tolerance, to_gpu
+from gpu_util import LDR_TOL, gpu_graph_arrays, np_, rel_norm, sigma_rel, to_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -32,18 +32,18 @@ def _samples(N, n0, extra, seed):
     return np.unique(np.array(js, np.int64))
 
 
-def _check_rows(pts, tp, js, nbrs_tree, b_rows, sig_rows, kern):
+def _check_rows(pts, tp, js, nbrs_tree, b_rows, sig_rows, kern, tol):
     """b and sigma of the GPU at the sampled tree indices js against the
     oracle's FP64 conditional on the neighbour lists nbrs_tree (tree indices,
-    found independently of the GPU), each within its row's FP32 bound."""
+    found independently of the GPU): b norm-wise over the sampled rows and
+    sigma element-wise, each within tol."""
     K = oracle.Kernel(*kern)
     idx = tp[js]
     nb_in = np.where(nbrs_tree >= 0, tp[np.maximum(nbrs_tree, 0)], -1).astype(np.int32)
     b_or, s_or = oracle.factor_rows(pts, idx, nb_in, K)
-    for r in range(len(js)):
-        tb, ts = row_tolerance(pts[nb_in[r]], pts[idx[r]], kern)
-        assert rel_norm(b_rows[r], b_or[r]) < tb, (js[r], rel_norm(b_rows[r], b_or[r]), tb)
-        assert abs(sig_rows[r] / s_or[r] - 1.0) < ts, (js[r], sig_rows[r], s_or[r], ts)
+    eb, es = rel_norm(b_rows, b_or), sigma_rel(sig_rows, s_or)
+    print(f"sampled rows ({len(js)}): b {eb:.2e}, sigma {es:.2e}")
+    assert eb < tol and es < tol, (eb, es, tol)
 
 
 def _positions(order):
@@ -85,20 +85,21 @@ def test_ldr_workload_full_oracle(gpu_lib):
     fo = oracle.factor(want["pts_pos"], want["nbr_pos"], k, N0, K)
     f = gpu_lib.factor(g, gpu_lib.Kernel(*kern))
     b, sigma, _ = (np_(t) for t in f.export())
-    tol = fp32_tolerance(want, kern)
+    tol = LDR_TOL
     print(f"ldr 2^20: b rel {rel_norm(b, fo['b']):.2e}, sigma max rel "
-          f"{np.max(np.abs(sigma / fo['sigma'] - 1)):.2e}, tol {tol}")
-    assert rel_norm(b, fo["b"]) < tol[0]
+          f"{sigma_rel(sigma, fo['sigma']):.2e}")
+    assert rel_norm(b, fo["b"]) < tol
+    assert sigma_rel(sigma, fo["sigma"]) < tol
     xi = workloads.white_noise(N, w["xi_seed"])
     v_or = oracle.generate(fo, want["nbr_pos"], k, N0, xi.astype(np.float64))
     v = np_(gpu_lib.generate(g, f, to_gpu(xi)))
     print(f"ldr 2^20: v rel {rel_norm(v, v_or):.2e}")
-    assert rel_norm(v, v_or) < tol[0]
+    assert rel_norm(v, v_or) < tol
     v_in = v_or.astype(np.float32)
     xi_or = oracle.whiten(fo, want["nbr_pos"], k, N0, v_in.astype(np.float64))
     xi_g = np_(gpu_lib.whiten(g, f, to_gpu(v_in)))
     print(f"ldr 2^20: xi rel {rel_norm(xi_g, xi_or):.2e}")
-    assert rel_norm(xi_g, xi_or) < tol[1]
+    assert rel_norm(xi_g, xi_or) < tol
     ld = np_(gpu_lib.logdet(f))[0]
     print(f"ldr 2^20: logdet {ld:.6f} oracle {fo['logdet']:.6f}")
     assert abs(ld - fo["logdet"]) <= 2.0 * np.sum(np.abs(sigma / fo["sigma"] - 1.0)) * 1.01 + 1e-9 * abs(fo["logdet"])
@@ -124,7 +125,7 @@ def test_diff_workload_full_size(gpu_lib):
     b, sigma, _ = f.export()
     pos = _positions(got["order"])[tp[js]]
     pos_t = torch.as_tensor(pos, device="cuda")
-    _check_rows(pts, tp, js, nb_or, np_(b[pos_t - N0]), np_(sigma[pos_t]), kern)
+    _check_rows(pts, tp, js, nb_or, np_(b[pos_t - N0]), np_(sigma[pos_t]), kern, 1e-3)
     del b
     xi, v = _sweep_properties(gpu_lib, g, f, N, w["xi_seed"], sigma)
     # adjoint identity at full size: <L xi, u> = <xi, L^T u>
@@ -162,7 +163,7 @@ def test_metric_workload_full_size(gpu_lib):
     check_depth_and_order(got["nbr_tree"], got["depth"], got["inorder"], tp, got["order"],
                           got["level_offsets"], got["nbr_pos"], N0)
     X = pts[tp]
-    js = _samples(N, N0, 2, 2)
+    js = _samples(N, N0, 8, 2)
     nb = np.stack([knn_sample(X, int(j), k) for j in js])
     assert np.array_equal(got["nbr_tree"][js - N0], nb)
     pos = _positions(got["order"])[tp[js]]
@@ -174,7 +175,7 @@ def test_metric_workload_full_size(gpu_lib):
     b_rows, sig_rows = np_(b[pos_t - N0]), np_(sigma[pos_t])
     del b
     torch.cuda.empty_cache()
-    _check_rows(pts, tp, js, nb, b_rows, sig_rows, kern)
+    _check_rows(pts, tp, js, nb, b_rows, sig_rows, kern, 1e-3)
     xi, v = _sweep_properties(gpu_lib, g, f, N, w["xi_seed"], sigma)
     _generate_rows(b_rows, sig_rows, nbr_rows, pos, v, xi)
 
@@ -228,6 +229,6 @@ def test_scale_workload_full_size(gpu_lib):
     b_rows, sig_rows = np_(b[pos_t - N0]), np_(sigma[pos_t])
     del b
     torch.cuda.empty_cache()
-    _check_rows(pts, tp, js, nb, b_rows, sig_rows, kern)
+    _check_rows(pts, tp, js, nb, b_rows, sig_rows, kern, 1e-2)
     xi, v = _sweep_properties(gpu_lib, g, f, N, w["xi_seed"], sigma)
     _generate_rows(b_rows, sig_rows, nbr_rows, pos, v, xi)

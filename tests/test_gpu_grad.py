@@ -1,14 +1,15 @@
 """GPU adjoints (Sec. 2.3) against the FP64 oracle's closed-form gradients on
-the same seeded inputs.  Vector cotangents: norm-wise relative 1e-4.  Kernel
-parameter gradients: every component within 2e-3 of the largest one (FP32
-recompute of the k x k factors, summed over all points in FP64)."""
+the same seeded inputs.  Vector cotangents and point gradients: norm-wise
+relative 1e-4.  Kernel parameter gradients: every component within 1e-4 of
+itself (FP32 recompute of the k x k factors, summed over all points in
+FP64)."""
 import numpy as np
 import pytest
 import torch
 
 import oracle
 import workloads
-from gpu_util import fp32_tolerance, np_, rel_norm, to_gpu
+from gpu_util import TOL, assert_theta, np_, rel_norm, theta_rel, to_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -19,6 +20,8 @@ CASES = [
     # the same kernel at k = 16 (one thread per point in the recompute)
     ("uniform", 4096, 16, (3, 1.0, 0.03, 1e-4)),
     ("gaussian", 3000, 16, (1, 1.0, 0.1, 1e-6)),
+    # theta_bar of this case is held to 1e-3 (THETA_TOL): its sigma2
+    # component is a difference of terms ~20x larger than itself
     ("ldr", 3000, 5, (2, 1.2, 0.1, 1e-3)),
     # 32 < k <= 64: one warp per point, the factor in shared memory
     ("uniform", 3000, 48, (1, 1.0, 0.03, 1e-4)),
@@ -36,15 +39,16 @@ def _setup(gg, kind, N, k, kern):
     return g, f, want, fo, K
 
 
-def _theta_close(got, want, tol=1e-4):
-    scale = np.max(np.abs(want))
-    assert np.all(np.abs(got - want) <= max(2e-3, 20 * tol) * scale), (got, want)
+def _theta_close(got, want, tol=TOL):
+    assert_theta(got, want, tol)
+
+
+# named cases whose theta_bar is held to 1e-3 instead of 1e-4
+THETA_TOL = {("ldr", 3000, 5, (2, 1.2, 0.1, 1e-3)): 1e-3}
 
 
 def _tol(want, kern, k):
-    """1e-4, or the FP32 conditioning bound when the kernel is too smooth for
-    it (the large-dynamic-range cloud's dense core)."""
-    return fp32_tolerance(want, kern)[1]
+    return TOL
 
 
 @pytest.mark.parametrize("case", CASES)
@@ -56,8 +60,8 @@ def test_nll_gradient(gpu_lib, case):
     vbar_or, tb_or = oracle.nll_grad(want, K, v.astype(np.float64))
     vbar, tb = gpu_lib.nll_backward(g, f, to_gpu(v))
     tol = _tol(want, kern, k)
-    assert rel_norm(np_(vbar), vbar_or) < tol
-    _theta_close(np_(tb), tb_or, tol)
+    assert rel_norm(np_(vbar), vbar_or) < tol, rel_norm(np_(vbar), vbar_or)
+    _theta_close(np_(tb), tb_or, THETA_TOL.get(case, tol))
 
 
 @pytest.mark.parametrize("case", CASES)
@@ -75,8 +79,8 @@ def test_whiten_vjp(gpu_lib, case):
     xi = gpu_lib.whiten(g, f, to_gpu(v))
     vbar, tb = gpu_lib.whiten_backward(g, f, to_gpu(v), xi, to_gpu(xibar), 0.7)
     tol = _tol(want, kern, k)
-    assert rel_norm(np_(vbar), a["vbar"]) < tol
-    _theta_close(np_(tb), tb_or, tol)
+    assert rel_norm(np_(vbar), a["vbar"]) < tol, rel_norm(np_(vbar), a["vbar"])
+    _theta_close(np_(tb), tb_or, THETA_TOL.get(case, tol))
 
 
 @pytest.mark.parametrize("case", CASES)
@@ -94,8 +98,8 @@ def test_generate_vjp(gpu_lib, case):
     v = gpu_lib.generate(g, f, to_gpu(xi))
     xibar, tb = gpu_lib.generate_backward(g, f, to_gpu(xi), v, to_gpu(vbar))
     tol = _tol(want, kern, k)
-    assert rel_norm(np_(xibar), a["xibar"]) < tol
-    _theta_close(np_(tb), tb_or, tol)
+    assert rel_norm(np_(xibar), a["xibar"]) < tol, rel_norm(np_(xibar), a["xibar"])
+    _theta_close(np_(tb), tb_or, THETA_TOL.get(case, tol))
 
 
 def test_thetabar_accumulates(gpu_lib):
@@ -120,19 +124,20 @@ def _max_cond(want, K, k, rows=200):
     return out
 
 
-def test_ill_conditioned_kernel_error_scales_with_condition(gpu_lib):
-    """A very smooth kernel (SE, l = 0.3 on a unit-Gaussian cloud) makes K_cc
-    ill conditioned; FP32 kernel evaluation perturbs K by ~2^-24 relative, so
-    the gradient error is bounded by ~cond(K_cc) 2^-24 rather than 1e-4."""
+def test_ill_conditioned_kernel(gpu_lib):
+    """A very smooth kernel (SE, l = 0.3 on a unit-Gaussian cloud of 3000
+    points: cond(K_cc) ~1e5): vbar to the stated 1e-4, theta_bar to 1e-3 per
+    component (its sigma2 component is a difference of terms ~4000x larger
+    than itself)."""
     g, f, want, fo, K = _setup(gpu_lib, "gaussian", 3000, 16, (3, 1.0, 0.3, 1e-4))
     cond = _max_cond(want, K, 16)
-    tol = max(1e-4, 4.0 * cond * 2.0 ** -24)
+    assert cond > 1e4
     v = oracle.generate(fo, want["nbr_pos"], 16, 64,
                         workloads.white_noise(3000, 61).astype(np.float64)).astype(np.float32)
     vbar_or, tb_or = oracle.nll_grad(want, K, v.astype(np.float64))
     vbar, tb = gpu_lib.nll_backward(g, f, to_gpu(v))
-    assert rel_norm(np_(vbar), vbar_or) < tol, (cond, tol)
-    assert np.all(np.abs(np_(tb) - tb_or) <= max(2e-3, tol * 10) * np.abs(tb_or).max())
+    assert rel_norm(np_(vbar), vbar_or) < TOL, (cond, rel_norm(np_(vbar), vbar_or))
+    _theta_close(np_(tb), tb_or, 1e-3)
 
 
 def test_autograd_functions_match_oracle(gpu_lib):
@@ -186,8 +191,8 @@ def test_nll_point_gradient(gpu_lib, case):
     pb_or = oracle.nll_grad_points(want, K, v.astype(np.float64))
     pb = np_(gpu_lib.nll_backward_points(g, f, to_gpu(v))).astype(np.float64)
     tol = _tol(want, kern, k)
-    assert rel_norm(pb, pb_or) < max(2e-3, 20 * tol)
-    assert np.all(np.abs(pb.sum(axis=0)) <= max(2e-3, 20 * tol) * np.abs(pb).sum())
+    assert rel_norm(pb, pb_or) < tol, rel_norm(pb, pb_or)
+    assert np.all(np.abs(pb.sum(axis=0)) <= tol * np.abs(pb).sum())
     # scaled cotangent
     pb2 = np_(gpu_lib.nll_backward_points(g, f, to_gpu(v), nllbar=-0.5)).astype(np.float64)
     assert rel_norm(pb2, -0.5 * pb) < 1e-6
@@ -198,9 +203,9 @@ def test_autograd_nll_with_points(gpu_lib):
     respect to v, theta and the [N, 2] points the graph was built from (the
     zero-padded third coordinate is dropped).  The plumbing (order, the
     upstream factor 2, the dropped coordinate) is checked against the direct
-    entry points to 1e-6; the values against the oracle within the FP32
-    conditioning bound of this cloud (2-D, smooth kernel: cond(K_cc) makes
-    the bound looser than 1e-4 here)."""
+    entry points to 1e-6; the values against the oracle to 1e-4 (theta_bar:
+    1e-3 per component; its sigma2 component is a difference of terms ~200x
+    larger than itself on this cloud)."""
     from paper_2606_11402_gb300 import autograd as ga
     N, k, kern = 2500, 8, (1, 1.0, 0.1, 1e-4)
     pts2 = workloads.uniform_cube(N, 81)[:, :2].copy()
@@ -224,7 +229,6 @@ def test_autograd_nll_with_points(gpu_lib):
     assert rel_norm(np_(P.grad), 2.0 * np_(pb)[:, :2]) < 1e-6
     vbar_or, tb_or = oracle.nll_grad(want, K, v.astype(np.float64))
     pb_or = oracle.nll_grad_points(want, K, v.astype(np.float64))
-    tol = fp32_tolerance(want, kern)[0]
-    assert rel_norm(np_(vt.grad), 2.0 * vbar_or) < tol
-    _theta_close(theta.grad.numpy(), 2.0 * tb_or, tol)
-    assert rel_norm(np_(P.grad), 2.0 * pb_or[:, :2]) < max(2e-3, 20 * tol)
+    assert rel_norm(np_(vt.grad), 2.0 * vbar_or) < TOL
+    _theta_close(theta.grad.numpy(), 2.0 * tb_or, 1e-3)
+    assert rel_norm(np_(P.grad), 2.0 * pb_or[:, :2]) < TOL, rel_norm(np_(P.grad), 2.0 * pb_or[:, :2])
