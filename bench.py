@@ -258,6 +258,8 @@ def differentiation_bench(stream, reps=3):
     b.record(stream)
     torch.cuda.synchronize()
     pts_ms = a.elapsed_time(b)
+    del f
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
     f2 = gg.factor(g, kern)
     torch.cuda.synchronize()
@@ -330,6 +332,9 @@ def run_ours(args):
     torch.cuda.synchronize()
     t_graph = time.perf_counter() - t0
     del pts
+    f = gg.factor(g, kern)  # first call loads the factor kernels
+    del f
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
     f = gg.factor(g, kern)
     torch.cuda.synchronize()

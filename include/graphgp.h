@@ -71,17 +71,21 @@ typedef struct {
   double nugget;      /* >= 0, added on the diagonal */
   double rescue_tol;  /* precision policy of the per-point conditionals (not
                          in the paper, which runs one precision).  Every
-                         conditional is factored in FP32; its relative error
-                         is estimated a priori as
-                           est = 2^-24 (K_00 / p_min) (K_00 / sigma_i^2)
-                         (p_min = smallest Cholesky pivot of K_cc; K_00 / p_min
-                         bounds cond(K_cc) from below, K_00 / sigma^2 is the
-                         cancellation in sigma^2 = K_ii - K_ic b).  A row with
-                         est > rescue_tol, a floored pivot or a non-finite
-                         result is recomputed in FP64.  0 = default 2^-10;
-                         < 0 = every conditional in FP64 (slow on GB300:
-                         FP64 runs at 1/64 of the FP32 rate).  Must be
-                         finite. */
+                         conditional is factored in FP32 (in increments of
+                         the field when its nearest neighbour is close, see
+                         graphgp_factor); its relative error is estimated a
+                         priori as
+                           est = 2^-20 max_j (M_jj / p_j)
+                                 (1 + 2^-8 Var(w) / sigma_i^2)
+                         (M the covariance the row factors, p_j its Cholesky
+                         pivots: a lower bound on M's scaled condition
+                         number; Var(w) / sigma_i^2 the cancellation in the
+                         conditional variance).  A row with est > rescue_tol,
+                         a floored pivot or a non-finite result is recomputed
+                         in FP64; so is the dense block when 2^-24 (K_00 /
+                         p_min)^2 exceeds it.  0 = default 2^-7; < 0 = every
+                         conditional in FP64 (slow on GB300: FP64 runs at a
+                         small fraction of the FP32 rate).  Must be finite. */
 } graphgp_kernel;
 
 typedef struct {
@@ -150,13 +154,19 @@ int graphgp_graph_load(const char* path, void* stream, graphgp_graph_t* out);
 void graphgp_graph_destroy(graphgp_graph_t g);
 
 /* ---- factor (Sec. 2.1, Eq. 2; Alg. 1) -----------------------------------
- * For every position i >= n0: K_cc, K_ci from kappa on the coordinates of
- * c(i) and i, L = chol(K_cc), y = L^-1 K_ci, b_i = L^-T y (the weights
- * K_ic K_cc^-1 of Eq. 2), sigma_i^2 = K_ii - y.y (compensated FP32),
- * sigma_i = sqrt.  Dense block: L0 = chol(K_00) over positions 0..n0-1 and
- * its inverse, sigma_i = L0_ii.  logdet = 2 sum_i log sigma_i is reduced in
- * FP64 from the stored FP32 sigma.  Pivots below 1e-7 * K_jj are clamped to
- * that value and counted (see graphgp_sync_status). */
+ * For every position i >= n0: the weights b_i = K_ic K_cc^-1 of Eq. 2 and
+ * sigma_i^2 = K_ii - K_ic K_cc^-1 K_ci, by a Cholesky factor in FP32 (sigma^2
+ * accumulated compensated).  Rows whose nearest neighbour is close (variogram
+ * g = kappa(0) - kappa(r) below kappa(0)/2) are factored in increments of
+ * the field centred on that neighbour, an exact change of variables whose
+ * covariances are sums of variogram values; the others in the covariance
+ * form.  Rows flagged by kern->rescue_tol are recomputed in FP64.  Dense
+ * block: L0 = chol(K_00) over positions 0..n0-1 and its inverse, sigma_i =
+ * L0_ii (FP64 when flagged).  logdet = 2 sum_i log sigma_i is reduced in FP64
+ * from the stored FP32 sigma.  Pivots below 1e-7 (kappa(0) + nugget) are
+ * clamped to that value and counted (see graphgp_sync_status).  Allocates
+ * stream-ordered scratch (a list of rows for the FP64 pass, FP64 work arrays
+ * of 2 n0^2 doubles). */
 int graphgp_factor(graphgp_graph_t g, const graphgp_kernel* kern, void* stream,
                    graphgp_factor_t* out);
 

@@ -53,7 +53,7 @@ class Kernel:
     lengthscale: float = 0.1
     nugget: float = 0.0
     # rows whose a-priori FP32 error estimate exceeds this are recomputed in
-    # FP64 (0 = library default 2^-10, negative = every row in FP64)
+    # FP64 (0 = library default 2^-7, negative = every row in FP64)
     rescue_tol: float = 0.0
 
     def _c(self) -> _Kernel:

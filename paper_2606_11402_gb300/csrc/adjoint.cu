@@ -483,15 +483,16 @@ __global__ void __launch_bounds__(128) factor_backward_wide_kernel(
   block_add3(tl, ts, tn, thetabar);
 }
 
-// FP64 backward of the rows the lane-group kernel handed over (rescue.cuh).
+// FP64 backward of the rows the per-row kernels handed over (rescue.cuh).
 template <int G, int KT>
 __global__ void __launch_bounds__(128) factor_backward_rescue_kernel(
     const float4* __restrict__ xs, const int32_t* __restrict__ nbr, int k, int kp, int64_t n0,
     KernF kf, int mode, const float* __restrict__ coef, float beta, const float* __restrict__ v,
     const float* __restrict__ xi, float* __restrict__ xibar_out, double* __restrict__ thetabar,
-    const int64_t* __restrict__ rows, const unsigned long long* __restrict__ count) {
+    const int64_t* __restrict__ rows, const unsigned long long* __restrict__ count,
+    unsigned long long cap) {
   double tl = 0.0, ts = 0.0, tn = 0.0;
-  const int64_t n = (int64_t)*count;
+  const int64_t n = (int64_t)(*count < cap ? *count : cap);
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
        r += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = rows[r];
@@ -519,7 +520,11 @@ template <int K, int KT>
 __global__ void __launch_bounds__(128) factor_backward_thread_kernel(
     const float4* __restrict__ xs, const int32_t* __restrict__ nbr, int64_t N, int k, int64_t n0,
     KernF kf, int mode, const float* __restrict__ coef, float beta, const float* __restrict__ v,
-    const float* __restrict__ xi, float* __restrict__ xibar_out, double* __restrict__ thetabar) {
+    const float* __restrict__ xi, float* __restrict__ xibar_out, double* __restrict__ thetabar,
+    int64_t* __restrict__ rescue_rows, unsigned long long* __restrict__ rescue_count,
+    unsigned long long rescue_cap) {
+  extern __shared__ __align__(16) unsigned char tstage[];
+  const ThreadStage<K> st(tstage);
   double tl = 0.0, ts = 0.0, tn = 0.0;
   const int64_t npts = N - n0;
   const float inv_s2 = 1.0f / kf.s2;
@@ -530,19 +535,15 @@ __global__ void __launch_bounds__(128) factor_backward_thread_kernel(
     const int4* row = reinterpret_cast<const int4*>(row_ptr);
     const float4 xq = __ldg(xs + i);
     PointRegs<K> p;
-    {
-      float4 x[K];
-#pragma unroll
-      for (int q = 0; q < K / 4; q++) {
-        const int4 c = __ldg(row + q);
-        x[4 * q] = __ldg(xs + c.x);
-        x[4 * q + 1] = __ldg(xs + c.y);
-        x[4 * q + 2] = __ldg(xs + c.z);
-        x[4 * q + 3] = __ldg(xs + c.w);
-      }
-      point_factor_thread<K, KT>(p, k, kf, x, xq);
-    }
+    stage_coords<K>(st, xs, row_ptr, k);
+    point_factor_thread<K, KT>(p, k, kf, st, xq);
     if (needs_rescue(p, k, kf)) {
+      // listed for factor_backward_rescue_kernel; recomputed here when the list is full
+      const unsigned long long slot = atomicAdd(rescue_count, 1ull);
+      if (slot < rescue_cap) {
+        rescue_rows[slot] = i;
+        continue;
+      }
       Row64<K> R;
       row_factor64<K, KT>(R, xs, row_ptr, k, xq, kf);
       const float sg = (float)R.sigma;
@@ -575,9 +576,9 @@ __global__ void __launch_bounds__(128) factor_backward_thread_kernel(
     // row sums in FP32 (at most k + 1 terms), added to the FP64 totals
     ts += sbar;  // Kbar_ii = sbar
     tn += sbar;
-    float4 x[K];
+    float4 x[K];  // the staged coordinates (padding: the point itself)
 #pragma unroll
-    for (int a = 0; a < K; a++) x[a] = a < k ? __ldg(xs + ca[a]) : xq;
+    for (int a = 0; a < K; a++) x[a] = a < k ? st.X[a * kThreadBlock] : xq;
 #pragma unroll
     for (int a = 0; a < K; a++) {
       if (a < k) {
@@ -632,7 +633,8 @@ int launch_factor_backward(graphgp_graph_t g, graphgp_factor_t f, int mode, cons
                                                      kf, mode, coef, beta, v, xi, xibar,     \
                                                      thetabar, rows, cnt);                   \
   factor_backward_rescue_kernel<G, KT><<<rgrid, 128, 0, s>>>(                               \
-      g->xs, g->nbr, g->k, g->kp, g->n0, kf, mode, coef, beta, v, xi, xibar, thetabar, rows, cnt)
+      g->xs, g->nbr, g->k, g->kp, g->n0, kf, mode, coef, beta, v, xi, xibar, thetabar, rows, cnt, \
+      (unsigned long long)npts)
   switch (f->kern.type) {
     case GRAPHGP_MATERN12: GGP_FB(GRAPHGP_MATERN12); break;
     case GRAPHGP_MATERN32: GGP_FB(GRAPHGP_MATERN32); break;
@@ -644,6 +646,8 @@ int launch_factor_backward(graphgp_graph_t g, graphgp_factor_t f, int mode, cons
   return GRAPHGP_OK;
 }
 
+constexpr int64_t kBackwardRescueMax = 1 << 20;  // rows listed for the FP64 backward
+
 template <int K>
 int launch_factor_backward_thread(graphgp_graph_t g, graphgp_factor_t f, int mode,
                                   const float* coef, float beta, const float* v, const float* xi,
@@ -652,10 +656,22 @@ int launch_factor_backward_thread(graphgp_graph_t g, graphgp_factor_t f, int mod
   if (npts <= 0) return GRAPHGP_OK;
   const unsigned grid = grid_for(npts, 128, 8);
   KernF kf = make_kernf(f->kern);
+  Scratch sc(s);
+  const unsigned long long cap = (unsigned long long)std::min<int64_t>(npts, kBackwardRescueMax);
+  int64_t* rows = nullptr;
+  unsigned long long* cnt = nullptr;
+  GGP_TRY(sc.alloc(&rows, cap));
+  GGP_TRY(sc.alloc(&cnt, 1));
+  GGP_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), s));
+  const unsigned rgrid = (unsigned)num_sms() * 2;
+  constexpr size_t smem = ThreadStage<K>::kBytes;
 #define GGP_FBT(KT)                                                                             \
-  factor_backward_thread_kernel<K, KT><<<grid, 128, 0, s>>>(g->xs, g->nbr, g->N, g->k, g->n0, kf, \
-                                                            mode, coef, beta, v, xi, xibar,      \
-                                                            thetabar)
+  GGP_CUDA(allow_dyn_smem(factor_backward_thread_kernel<K, KT>, smem));                         \
+  factor_backward_thread_kernel<K, KT><<<grid, kThreadBlock, smem, s>>>(                        \
+      g->xs, g->nbr, g->N, g->k, g->n0, kf, mode, coef, beta, v, xi, xibar, thetabar, rows, cnt, \
+      cap);                                                                                     \
+  factor_backward_rescue_kernel<K, KT><<<rgrid, 128, 0, s>>>(                                   \
+      g->xs, g->nbr, g->k, g->kp, g->n0, kf, mode, coef, beta, v, xi, xibar, thetabar, rows, cnt, cap)
   switch (f->kern.type) {
     case GRAPHGP_MATERN12: GGP_FBT(GRAPHGP_MATERN12); break;
     case GRAPHGP_MATERN32: GGP_FBT(GRAPHGP_MATERN32); break;
@@ -690,7 +706,8 @@ int launch_factor_backward_wide(graphgp_graph_t g, graphgp_factor_t f, int mode,
       g->xs, g->nbr, g->N, g->k, g->kp, g->n0, kf, mode, coef, beta, v, xi, xibar, thetabar,   \
       rows, cnt);                                                                              \
   factor_backward_rescue_kernel<kWideK, KT><<<rgrid, 128, 0, s>>>(                             \
-      g->xs, g->nbr, g->k, g->kp, g->n0, kf, mode, coef, beta, v, xi, xibar, thetabar, rows, cnt)
+      g->xs, g->nbr, g->k, g->kp, g->n0, kf, mode, coef, beta, v, xi, xibar, thetabar, rows, cnt,  \
+      (unsigned long long)npts)
   switch (f->kern.type) {
     case GRAPHGP_MATERN12: GGP_FBW(GRAPHGP_MATERN12); break;
     case GRAPHGP_MATERN32: GGP_FBW(GRAPHGP_MATERN32); break;
@@ -831,8 +848,8 @@ int run_generate_backward(graphgp_graph_t g, graphgp_factor_t f, const float* xi
   int n0 = g->n0;
   if (g->num_levels > 1) {
     GGP_CUDA(cudaMemsetAsync(g->level_bar, 0, g->num_levels * sizeof(uint32_t), s));
-    static int max_grid = 0;
-    if (!max_grid) max_grid = coop_grid(generate_adjoint_kernel, 256);
+    static int max_grid_dev[kMaxDevices] = {};
+    const int max_grid = coop_grid_cached(max_grid_dev, generate_adjoint_kernel, 256);
     int grid = (int)std::min<int64_t>(max_grid, std::max<int64_t>((g->max_level_size + 255) / 256, 1));
     LevelBarrier lb{g->level_bar, g->err, g->max_spin};
     const int64_t* rp = g->csr.rowptr;

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "graphgp.h"
+#include "variogram_poly.cuh"
 
 namespace ggp {
 
@@ -177,8 +178,11 @@ struct KernF {
 };
 
 // Default per-row error estimate above which a conditional is recomputed in
-// FP64 (rescue.cuh): 2^-10, about 1e-3.
-constexpr double kDefaultRescueTol = 0.0009765625;
+// FP64 (rescue.cuh): 2^-7.  The estimate is conservative: on the measured
+// workloads the element-wise sigma error stays below 1e-3 at this setting,
+// and it sends 0.05 % of the headline cloud's rows, 0.3 % of a clustered
+// cloud's and 8 % of the nugget-free large-dynamic-range cloud's to FP64.
+constexpr double kDefaultRescueTol = 0.0078125;
 
 template <int KT>
 __device__ __forceinline__ float kappa_d2(const KernF& p, float d2) {
@@ -203,67 +207,39 @@ __device__ __forceinline__ float kappa_d2(const KernF& p, float d2) {
 // where kappa(r) is close to kappa(0) and 1 - kappa(r)/kappa(0) computed from
 // kappa would keep none of its digits.  The increment form of the per-point
 // factors (pointfactor.cuh) is built from these values.  Below a switch point
-// gamma comes from a series with positive terms (or alternating terms of
-// decreasing size), above it from the closed form, which there loses at most
-// a small factor to cancellation:
+// gamma is a product of positive factors, one of them a short polynomial
+// (variogram_poly.cuh) for a function without cancellation; above it the
+// closed form, which there loses at most a small factor to cancellation:
 //   SE (u = r^2 / 2l^2), Matern-1/2 (u = r/l), u < 1/2:
-//       1 - e^-u = u (1 - u/2 + u^2/6 - ...)            (closed form: <= 2.6x)
+//       1 - e^-u = u psi(u),  psi(u) = (1 - e^-u) / u     (closed form: <= 2.6x)
 //   Matern-3/2, a = sqrt3 r/l < 1:
-//       1 - (1 + a) e^-a = e^-a sum_{n>=2} a^n/n!       (closed form: <= 2.8x)
+//       1 - (1 + a) e^-a = a^2 phi(a) e^-a,  phi(a) = (e^a - 1 - a) / a^2
+//                                                        (closed form: <= 2.8x)
 //   Matern-5/2, a = sqrt5 r/l < 2:
-//       1 - (1 + a + a^2/3) e^-a = e^-a (a^2/6 + sum_{n>=3} a^n/n!)  (<= 2.4x)
-// The series are cut where their remainder falls below 2^-28 of the value.
-__host__ __device__ constexpr double inv_factorial(int n) {
-  return n <= 1 ? 1.0 : inv_factorial(n - 1) / n;
-}
-
-// sum_{n=N..NMAX} a^(n-N) / n!, Horner with compile-time coefficients.
-template <int N, int NMAX>
-__device__ __forceinline__ float exp_tail_series(float a) {
-  constexpr float c = (float)inv_factorial(N);
-  if constexpr (N == NMAX) {
-    return c;
-  } else {
-    return fmaf(exp_tail_series<N + 1, NMAX>(a), a, c);
-  }
-}
-
-// sum_{n=N..NMAX} (-1)^(n-N) u^(n-N) / n!
-template <int N, int NMAX>
-__device__ __forceinline__ float exp_alt_series(float u) {
-  constexpr float c = (float)inv_factorial(N);
-  if constexpr (N == NMAX) {
-    return c;
-  } else {
-    return fmaf(-exp_alt_series<N + 1, NMAX>(u), u, c);
-  }
-}
-
+//       1 - (1 + a + a^2/3) e^-a = a^2 phi(a) e^-a,
+//       phi(a) = (e^a - 1 - a - a^2/3) / a^2              (closed form: <= 2.4x)
 struct KG {
   float k, g;  // kappa(r), gamma(r)
 };
 
 // kappa and gamma from one exponential (the per-point factors pick one of
-// the two per row).  The closed form of gamma is used at and above the
-// switch point, the series below it.
+// the two per row).
 template <int KT>
 __device__ __forceinline__ KG kappa_gamma_d2(const KernF& p, float d2) {
   if (KT == GRAPHGP_SQEXP || KT == GRAPHGP_MATERN12) {
     const float u = KT == GRAPHGP_SQEXP ? 0.5f * d2 * p.inv_ell * p.inv_ell : sqrtf(d2) * p.inv_ell;
     const float e = expf(-u);
-    return KG{p.s2 * e, p.s2 * (u < 0.5f ? u * exp_alt_series<1, 11>(u) : 1.0f - e)};
+    return KG{p.s2 * e, p.s2 * (u < 0.5f ? u * poly_exp1(u) : 1.0f - e)};
   } else if (KT == GRAPHGP_MATERN32) {
     const float a = 1.7320508075688772f * sqrtf(d2) * p.inv_ell;
     const float e = expf(-a);
     const float pe = (1.0f + a) * e;
-    return KG{p.s2 * pe, p.s2 * (a < 1.0f ? a * a * fmaf(a, exp_tail_series<3, 12>(a), 0.5f) * e
-                                           : 1.0f - pe)};
+    return KG{p.s2 * pe, p.s2 * (a < 1.0f ? a * a * poly_m32(a) * e : 1.0f - pe)};
   } else {
     const float a = 2.2360679774997896f * sqrtf(d2) * p.inv_ell;
     const float e = expf(-a);
     const float pe = (1.0f + a + a * a * (1.0f / 3.0f)) * e;
-    return KG{p.s2 * pe, p.s2 * (a < 2.0f ? a * a * fmaf(a, exp_tail_series<3, 17>(a), 1.0f / 6.0f) * e
-                                           : 1.0f - pe)};
+    return KG{p.s2 * pe, p.s2 * (a < 2.0f ? a * a * poly_m52(a) * e : 1.0f - pe)};
   }
 }
 
@@ -311,15 +287,24 @@ inline KernF make_kernf(const graphgp_kernel& k) {
   return p;
 }
 
+// Device-dependent launch sizes are cached per device index.
+constexpr int kMaxDevices = 64;
+
+inline int current_device() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  return (dev >= 0 && dev < kMaxDevices) ? dev : 0;
+}
+
 inline int num_sms() {
-  static int n = 0;
-  if (!n) {
-    int dev = 0;
-    cudaGetDevice(&dev);
+  static int cache[kMaxDevices] = {};
+  const int dev = current_device();
+  if (!cache[dev]) {
+    int n = 0;
     cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    if (n <= 0) n = 1;
+    cache[dev] = n > 0 ? n : 1;
   }
-  return n;
+  return cache[dev];
 }
 
 // Kernels whose dynamic shared memory grows with the number of depth levels

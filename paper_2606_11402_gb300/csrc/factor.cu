@@ -108,25 +108,18 @@ __global__ void __launch_bounds__(128) point_factor_thread_kernel(
     const float4* __restrict__ xs, const int32_t* __restrict__ nbr, int64_t N, int k, int64_t n0,
     KernF kf, float* __restrict__ b_out, float* __restrict__ sigma_out,
     double* __restrict__ logdet, unsigned long long* __restrict__ not_pd, RescueList rl) {
+  extern __shared__ __align__(16) unsigned char tstage[];
+  const ThreadStage<K> st(tstage);
   LogAcc acc;
   unsigned long long clamped_rows = 0;
   const int64_t npts = N - n0;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < npts;
        t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = n0 + t;
-    const int4* row = reinterpret_cast<const int4*>(nbr + t * K);
-    float4 x[K];
-#pragma unroll
-    for (int q = 0; q < K / 4; q++) {
-      const int4 c = __ldg(row + q);
-      x[4 * q] = __ldg(xs + c.x);
-      x[4 * q + 1] = __ldg(xs + c.y);
-      x[4 * q + 2] = __ldg(xs + c.z);
-      x[4 * q + 3] = __ldg(xs + c.w);
-    }
+    stage_coords<K>(st, xs, nbr + t * K, k);
     PointRegs<K> p;
     const float4 xq = __ldg(xs + i);
-    point_factor_thread<K, KT>(p, k, kf, x, xq);
+    point_factor_thread<K, KT>(p, k, kf, st, xq);
     if (needs_rescue(p, k, kf)) {
       if (rl.defer(i)) continue;
       rescue_thread<K, KT>(p, xs, nbr + t * K, k, xq, kf);
@@ -538,10 +531,12 @@ template <int K>
 int launch_point_thread(int type, graphgp_graph_t g, graphgp_factor_t f, const KernF& kf,
                         const RescueList& rl, cudaStream_t s) {
   const int64_t npts = g->N - g->n0;
-  const unsigned grid = grid_for(npts, 128, 8);
-#define GGP_PT(KT)                                                                       \
-  point_factor_thread_kernel<K, KT><<<grid, 128, 0, s>>>(g->xs, g->nbr, g->N, g->k, g->n0, kf, \
-                                                         f->b, f->sigma, f->logdet, f->not_pd, rl)
+  const unsigned grid = grid_for(npts, kThreadBlock, 8);
+  constexpr size_t smem = ThreadStage<K>::kBytes;
+#define GGP_PT(KT)                                                                            \
+  GGP_CUDA(allow_dyn_smem(point_factor_thread_kernel<K, KT>, smem));                          \
+  point_factor_thread_kernel<K, KT><<<grid, kThreadBlock, smem, s>>>(                         \
+      g->xs, g->nbr, g->N, g->k, g->n0, kf, f->b, f->sigma, f->logdet, f->not_pd, rl)
   switch (type) {
     case GRAPHGP_MATERN12: GGP_PT(GRAPHGP_MATERN12); break;
     case GRAPHGP_MATERN32: GGP_PT(GRAPHGP_MATERN32); break;

@@ -58,21 +58,12 @@ __device__ __forceinline__ float dot_stored_order(const float (&b)[K], const int
 }
 
 template <int K, int KT>
-__device__ __forceinline__ void factor_at(PointRegs<K>& p, const float4* __restrict__ xs,
-                                          const int32_t* row, int64_t i, int k, const KernF& kf) {
+__device__ __forceinline__ void factor_at(PointRegs<K>& p, const ThreadStage<K>& st,
+                                          const float4* __restrict__ xs, const int32_t* row,
+                                          int64_t i, int k, const KernF& kf) {
   const float4 xq = __ldg(xs + i);
-  {
-    float4 x[K];
-#pragma unroll
-    for (int q = 0; q < K / 4; q++) {
-      const int4 c = __ldg(reinterpret_cast<const int4*>(row) + q);
-      x[4 * q] = __ldg(xs + c.x);
-      x[4 * q + 1] = __ldg(xs + c.y);
-      x[4 * q + 2] = __ldg(xs + c.z);
-      x[4 * q + 3] = __ldg(xs + c.w);
-    }
-    point_factor_thread<K, KT>(p, k, kf, x, xq);
-  }
+  stage_coords<K>(st, xs, row, k);
+  point_factor_thread<K, KT>(p, k, kf, st, xq);
   if (needs_rescue(p, k, kf)) rescue_thread<K, KT>(p, xs, row, k, xq, kf);
 }
 
@@ -86,6 +77,8 @@ __global__ void __launch_bounds__(128) whiten_fused_kernel(
     const float4* __restrict__ xs, const int32_t* __restrict__ nbr, int64_t N, int k, int64_t n0,
     KernF kf, const float* __restrict__ v, float* __restrict__ xi, double* __restrict__ sq,
     double* __restrict__ logdet, unsigned long long* __restrict__ not_pd) {
+  extern __shared__ __align__(16) unsigned char tstage[];
+  const ThreadStage<K> stg(tstage);
   const uint64_t pol_v = l2_evict_last();
   LogAcc lacc;
   double local = 0.0;
@@ -96,7 +89,7 @@ __global__ void __launch_bounds__(128) whiten_fused_kernel(
     const int64_t i = n0 + t;
     const int32_t* row = nbr + t * K;
     PointRegs<K> p;
-    factor_at<K, KT>(p, xs, row, i, k, kf);
+    factor_at<K, KT>(p, stg, xs, row, i, k, kf);
     const float acc = dot_stored_order<K, false>(p.y, row, v, pol_v);
     const float out = (ld_keep_f(v + i, pol_v) - acc) / p.sigma;
     xi[i] = out;
@@ -115,6 +108,8 @@ __global__ void __launch_bounds__(128) generate_fused_kernel(
     const float* __restrict__ xi, float* v, const int64_t* __restrict__ level_off,
     int num_levels, LevelBarrier lb, unsigned long long* __restrict__ not_pd) {
   __shared__ int s_flag;
+  extern __shared__ __align__(16) unsigned char tstage[];
+  const ThreadStage<K> stg(tstage);
   const uint64_t pol_v = l2_evict_last();
   unsigned long long clamped = 0;
   for (int l = 1; l < num_levels; l++) {
@@ -129,7 +124,7 @@ __global__ void __launch_bounds__(128) generate_fused_kernel(
       const bool active = q < hi;
       const int32_t* row = nbr + (active ? q - n0 : 0) * K;
       PointRegs<K> p;
-      if (active) factor_at<K, KT>(p, xs, row, q, k, kf);
+      if (active) factor_at<K, KT>(p, stg, xs, row, q, k, kf);
       // the level's inputs are complete once every block arrived at l - 1
       if (st == 0 && l > 1 && lb.wait(l - 1, gridDim.x, &s_flag)) return;
       if (active) {
@@ -176,10 +171,12 @@ int launch_whiten_fused(graphgp_graph_t g, int type, const KernF& kf, const floa
                         double* sq, double* logdet, unsigned long long* not_pd, cudaStream_t s) {
   const int64_t npts = g->N - g->n0;
   if (npts <= 0) return GRAPHGP_OK;
-  const unsigned grid = grid_for(npts, 128, 8);
-#define GGP_WF(KT)                                                                              \
-  whiten_fused_kernel<K, KT><<<grid, 128, 0, s>>>(g->xs, g->nbr, g->N, g->k, g->n0, kf, v, xi, sq, \
-                                                  logdet, not_pd)
+  const unsigned grid = grid_for(npts, kThreadBlock, 8);
+  constexpr size_t smem = ThreadStage<K>::kBytes;
+#define GGP_WF(KT)                                                                            \
+  GGP_CUDA(allow_dyn_smem(whiten_fused_kernel<K, KT>, smem));                                 \
+  whiten_fused_kernel<K, KT><<<grid, kThreadBlock, smem, s>>>(g->xs, g->nbr, g->N, g->k, g->n0, \
+                                                              kf, v, xi, sq, logdet, not_pd)
   switch (type) {
     case GRAPHGP_MATERN12: GGP_WF(GRAPHGP_MATERN12); break;
     case GRAPHGP_MATERN32: GGP_WF(GRAPHGP_MATERN32); break;
@@ -194,8 +191,10 @@ int launch_whiten_fused(graphgp_graph_t g, int type, const KernF& kf, const floa
 template <int K, int KT>
 int launch_generate_fused_kt(graphgp_graph_t g, const KernF& kf, const float* xi, float* v,
                              unsigned long long* not_pd, cudaStream_t s) {
-  static int max_grid = 0;
-  if (!max_grid) max_grid = coop_grid(generate_fused_kernel<K, KT>, 128);
+  constexpr size_t smem = ThreadStage<K>::kBytes;
+  GGP_CUDA(allow_dyn_smem(generate_fused_kernel<K, KT>, smem));
+  static int max_grid_dev[kMaxDevices] = {};
+  const int max_grid = coop_grid_cached(max_grid_dev, generate_fused_kernel<K, KT>, kThreadBlock, smem);
   const int64_t want = (g->max_level_size + 127) / 128;
   const int grid = (int)std::min<int64_t>(max_grid, std::max<int64_t>(want, 1));
   GGP_CUDA(cudaMemsetAsync(g->level_bar, 0, g->num_levels * sizeof(uint32_t), s));
@@ -209,7 +208,7 @@ int launch_generate_fused_kt(graphgp_graph_t g, const KernF& kf, const float* xi
   void* args[] = {(void*)&xs, (void*)&nbr, (void*)&k, (void*)&n0, (void*)&kf, (void*)&xi,
                   (void*)&v,  (void*)&lo,  (void*)&nl, (void*)&lb, (void*)&not_pd};
   GGP_CUDA(cudaLaunchCooperativeKernel((const void*)generate_fused_kernel<K, KT>, dim3(grid),
-                                       dim3(128), args, 0, s));
+                                       dim3(kThreadBlock), args, smem, s));
   return GRAPHGP_OK;
 }
 

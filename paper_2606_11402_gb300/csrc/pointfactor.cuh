@@ -27,9 +27,8 @@
 //
 // A pivot at or below 1e-7 of kappa(0) + nugget is raised to that floor and
 // flagged; so is sigma^2.  max_ratio = max_j M_jj / pivot_j (pivot after the
-// floor) bounds the scaled
-// condition number of M from below; with Var(w) / sigma^2 (the cancellation
-// in sigma^2) it forms the row's error estimate (rescue.cuh).
+// floor) bounds the scaled condition number of M from below and gives the
+// row's error estimate (rescue.cuh).
 //
 // Group form: a group of G lanes of one warp (G = 8, 16 or 32 >= k), lane a
 // holding row a of M in registers.  Left-looking Cholesky: at step j every
@@ -106,7 +105,7 @@ struct PointState {
   float b_own;     // b_a (covariance-form weight of neighbour a)
   float sigma;     // conditional standard deviation (same on all lanes)
   bool clamped;    // a pivot was floored (same on all lanes)
-  float max_ratio; // max_j M_jj / pivot_j before flooring (same on all lanes)
+  float max_ratio; // max_j M_jj / pivot_j (same on all lanes)
   float varw;      // Var(w) (same on all lanes)
   bool inc;        // increment form (same on all lanes)
 };
@@ -290,7 +289,7 @@ struct PointRegs {
   float y[K];                // m, y = L^-1 m, beta = L^-T y, then b (zero for a >= k)
   float sigma;
   bool clamped;
-  float max_ratio;           // max_j M_jj / pivot_j before flooring
+  float max_ratio;           // max_j M_jj / pivot_j
   float varw;                // Var(w)
   bool inc;                  // increment form
   // 1 / L_jj, recomputed where needed (the same correctly rounded quotient)
@@ -315,32 +314,79 @@ __device__ __forceinline__ float schur_value(const PointRegs<K>& p) {
   return tv + t2;
 }
 
+// Shared-memory staging of the one-thread-per-point kernels (blocks of
+// kThreadBlock threads).  Evaluating the kernel values of a conditional
+// fully unrolled, with the whole factor live in registers, made the code
+// larger than the instruction cache (ncu: "no instruction" was the largest
+// stall).  The thread instead stages its k neighbour coordinates and then
+// its k(k-1)/2 + k kernel values in shared memory in a rolled loop, and the
+// unrolled factor reads them back.  Entry e of thread t sits at
+// [e * kThreadBlock + t] (consecutive threads, consecutive words).
+constexpr int kThreadBlock = 128;
+
+template <int K>
+struct ThreadStage {
+  static constexpr int kPairs = K * (K - 1) / 2;            // (a, c), c < a
+  static constexpr int kEntries = kPairs + K;                // and (a, i)
+  static constexpr size_t kBytes = (size_t)kThreadBlock * (16 * K + 4 * kEntries);
+  float4* X;  // neighbour coordinates, X[a * kThreadBlock]
+  float* E;   // kernel values, E[e * kThreadBlock]
+  __device__ __forceinline__ ThreadStage(unsigned char* smem) {
+    X = reinterpret_cast<float4*>(smem) + threadIdx.x;
+    E = reinterpret_cast<float*>(smem + (size_t)16 * K * kThreadBlock) + threadIdx.x;
+  }
+};
+
+__host__ __device__ constexpr int pair_ix(int a, int c) { return a * (a - 1) / 2 + c; }
+
+// Loads the k neighbour coordinates of a row (int4 index loads, float4
+// gathers) into the stage; entries k..K-1 are not written.
+template <int K>
+__device__ __forceinline__ void stage_coords(const ThreadStage<K>& st,
+                                             const float4* __restrict__ xs,
+                                             const int32_t* __restrict__ row, int k) {
+#pragma unroll
+  for (int q = 0; q < K / 4; q++) {
+    if (4 * q >= k) break;
+    const int4 c = __ldg(reinterpret_cast<const int4*>(row) + q);
+    st.X[(4 * q) * kThreadBlock] = __ldg(xs + c.x);
+    if (4 * q + 1 < k) st.X[(4 * q + 1) * kThreadBlock] = __ldg(xs + c.y);
+    if (4 * q + 2 < k) st.X[(4 * q + 2) * kThreadBlock] = __ldg(xs + c.z);
+    if (4 * q + 3 < k) st.X[(4 * q + 3) * kThreadBlock] = __ldg(xs + c.w);
+  }
+}
+
+// The factor of the row whose coordinates stage_coords put in `st`.
 template <int K, int KT>
 __device__ __forceinline__ void point_factor_thread(PointRegs<K>& p, int k, const KernF& kf,
-                                                    const float4 (&x)[K], float4 xq) {
+                                                    const ThreadStage<K>& st, float4 xq) {
   const float k0 = kf.s2 + kf.nug;
   const float nug = kf.nug;
-  const KG q0 = kappa_gamma_d2<KT>(kf, sqdist(x[0], xq));
+  const KG q0 = kappa_gamma_d2<KT>(kf, sqdist(st.X[0], xq));
   const bool inc = q0.g < 0.5f * kf.s2;
   p.inc = inc;
   // gamma (increment form) or kappa (covariance form) of every pair and of
-  // every neighbour with the point, last row first: coordinates x_a die as
-  // soon as row a is filled
-  static_for<0, K>([&](auto Ar) {
-    constexpr int a = K - 1 - decltype(Ar)::value;
+  // every neighbour with the point, in a rolled loop
+#pragma unroll 1
+  for (int a = 1; a < k; a++) {
+    const float4 xa = st.X[a * kThreadBlock];
+#pragma unroll 1
+    for (int c = 0; c < a; c++) {
+      const KG kg = kappa_gamma_d2<KT>(kf, sqdist(xa, st.X[c * kThreadBlock]));
+      st.E[pair_ix(a, c) * kThreadBlock] = inc ? kg.g : kg.k;
+    }
+    const KG kq = kappa_gamma_d2<KT>(kf, sqdist(xa, xq));
+    st.E[(ThreadStage<K>::kPairs + a) * kThreadBlock] = inc ? kq.g : kq.k;
+  }
+  // into registers; padding rows and columns (a >= k) are zero
+  static_for<1, K>([&](auto Ar) {
+    constexpr int a = decltype(Ar)::value;
     const bool real = a < k;
 #pragma unroll
-    for (int c = 0; c < a; c++) {
-      const KG kg = kappa_gamma_d2<KT>(kf, sqdist(x[a], x[c]));
-      p.L[tri(a, c)] = real ? (inc ? kg.g : kg.k) : 0.0f;
-    }
-    if constexpr (a == 0) {
-      p.y[0] = inc ? q0.g : q0.k;
-    } else {
-      const KG kg = kappa_gamma_d2<KT>(kf, sqdist(x[a], xq));
-      p.y[a] = real ? (inc ? kg.g : kg.k) : 0.0f;
-    }
+    for (int c = 0; c < a; c++) p.L[tri(a, c)] = real ? st.E[pair_ix(a, c) * kThreadBlock] : 0.0f;
+    p.y[a] = real ? st.E[(ThreadStage<K>::kPairs + a) * kThreadBlock] : 0.0f;
   });
+  p.y[0] = inc ? q0.g : q0.k;
   // M and m (column 0 last: in the increment form its entries are g_a0)
   const float e0i = p.y[0];
   static_for<1, K>([&](auto Ac) {

@@ -34,7 +34,7 @@ struct WideWarp {
 struct WideFactor {
   float sigma;
   bool clamped;     // a pivot or sigma^2 was floored
-  float max_ratio;  // max_j M_jj / pivot_j before flooring
+  float max_ratio;  // max_j M_jj / pivot_j
   float varw;       // Var(w)
   bool inc;         // increment form
 };

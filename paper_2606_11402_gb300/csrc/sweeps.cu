@@ -393,8 +393,8 @@ int launch_generate(graphgp_graph_t g, graphgp_factor_t f, const float* xi, floa
   if (a < z) {
     GGP_CUDA(cudaMemsetAsync(g->level_bar, 0, L * sizeof(uint32_t), s));
     auto kern = generate_kernel<KP, LANES, U>;
-    static int max_grid = 0;
-    if (!max_grid) max_grid = coop_grid(kern, kSweepThreads);
+    static int max_grid_dev[kMaxDevices] = {};
+    const int max_grid = coop_grid_cached(max_grid_dev, kern, kSweepThreads);
     int64_t want = (g->max_level_size + kSweepThreads - 1) / kSweepThreads;
     int grid = (int)std::min<int64_t>(max_grid, std::max<int64_t>(want, 1));
     LevelBarrier lb{g->level_bar, g->err, g->max_spin};

@@ -182,4 +182,12 @@ inline int coop_grid(F fn, int threads, size_t smem = 0) {
   return per_sm * num_sms();
 }
 
+// coop_grid remembered per device in `cache` (one slot per device index).
+template <class F>
+inline int coop_grid_cached(int (&cache)[kMaxDevices], F fn, int threads, size_t smem = 0) {
+  const int d = current_device();
+  if (!cache[d]) cache[d] = coop_grid(fn, threads, smem);
+  return cache[d];
+}
+
 }  // namespace ggp

@@ -7,7 +7,8 @@ bounds live in the test files.
 * differentiation kernel at N = 2^12 (uniform, k = 32, SE l = 0.03,
   nugget 1e-4),
 * large-dynamic-range workload at full size (N = 2^20, k = 16, Matern-3/2
-  l = 0.05, no nugget), against the complete oracle,
+  l = 0.05, no nugget), against the complete oracle, at the default rescue
+  threshold and at 2^-10,
 * headline workload (N = 2^26 unit Gaussian, k = 16, Matern-3/2 l = 0.1,
   nugget 1e-6): sampled factor rows against the oracle's conditional on the
   GPU's neighbour lists (themselves checked against brute force in
@@ -32,7 +33,7 @@ import workloads  # noqa: E402
 from gpu_util import np_, rel_norm, sigma_rel, theta_rel, to_gpu  # noqa: E402
 
 
-def full(pts, k, kern, n0=None, knn="brute", points=True):
+def full(pts, k, kern, n0=None, knn="brute", points=True, rescue_tol=0.0):
     out = {}
     want = oracle.build_graph(pts, k, n0, knn=knn)
     g = gg.build_graph(to_gpu(pts), k, n0=want["n0"])
@@ -40,7 +41,7 @@ def full(pts, k, kern, n0=None, knn="brute", points=True):
     assert np.array_equal(np_(order), want["order"]) and np.array_equal(np_(nbr), want["nbr_pos"])
     K = oracle.Kernel(*kern)
     fo = oracle.factor(want["pts_pos"], want["nbr_pos"], k, want["n0"], K)
-    f = gg.factor(g, gg.Kernel(*kern))
+    f = gg.factor(g, gg.Kernel(*kern, rescue_tol=rescue_tol))
     b, sigma, L0 = (np_(t) for t in f.export())
     out["b"] = rel_norm(b, fo["b"])
     out["sigma"] = sigma_rel(sigma, fo["sigma"])
@@ -105,6 +106,9 @@ def main():
          lambda: full(workloads.uniform_cube(4096, 4), 32, (3, 1.0, 0.03, 1e-4))),
         ("large dynamic range, N=2^20, k=16",
          lambda: full(workloads.ldr_cloud(1 << 20, 2), 16, (1, 1.0, 0.05, 0.0), 256, "tree", False)),
+        ("the same, rescue_tol 2^-10",
+         lambda: full(workloads.ldr_cloud(1 << 20, 2), 16, (1, 1.0, 0.05, 0.0), 256, "tree", False,
+                      2.0 ** -10)),
         ("headline, N=2^26, k=16 (3000 sampled rows)",
          lambda: sampled(workloads.unit_gaussian(1 << 26, 6), 16, (1, 1.0, 0.1, 1e-6))),
     ]

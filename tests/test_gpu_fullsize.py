@@ -18,7 +18,7 @@ import torch
 import oracle
 import workloads
 from fullsize import check_depth_and_order, check_tree, inorder_rank_of, inorder_ranks, knn_sample
-from gpu_util import LDR_TOL, gpu_graph_arrays, np_, rel_norm, sigma_rel, to_gpu
+from gpu_util import LDR_RESCUE, LDR_TOL, gpu_graph_arrays, np_, rel_norm, sigma_rel, to_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -83,7 +83,7 @@ def test_ldr_workload_full_oracle(gpu_lib):
         assert np.array_equal(got[key], want[key]), key
     K = oracle.Kernel(*kern)
     fo = oracle.factor(want["pts_pos"], want["nbr_pos"], k, N0, K)
-    f = gpu_lib.factor(g, gpu_lib.Kernel(*kern))
+    f = gpu_lib.factor(g, gpu_lib.Kernel(*kern, rescue_tol=LDR_RESCUE))
     b, sigma, _ = (np_(t) for t in f.export())
     tol = LDR_TOL
     print(f"ldr 2^20: b rel {rel_norm(b, fo['b']):.2e}, sigma max rel "

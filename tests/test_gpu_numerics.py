@@ -13,7 +13,7 @@ import torch
 
 import oracle
 import workloads
-from gpu_util import LDR_TOL, TOL, np_, rel_norm, sigma_rel, to_gpu
+from gpu_util import LDR_RESCUE, LDR_TOL, TOL, np_, rel_norm, sigma_rel, to_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -131,7 +131,8 @@ def test_fp64_rescue_of_ill_conditioned_rows(gpu_lib, k):
     N = 20_011
     pts = workloads.ldr_cloud(N, 33)
     kern = (1, 1.0, 0.05, 0.0)
-    g, f, want, fo, = _setup(gpu_lib, pts, k, kern, n0=256)
+    g, _, want, fo, = _setup(gpu_lib, pts, k, kern, n0=256)
+    f = gpu_lib.factor(g, gpu_lib.Kernel(*kern, rescue_tol=LDR_RESCUE))
     b, sigma, _ = (np_(t) for t in f.export())
     assert np.isfinite(b).all() and np.isfinite(sigma).all()
     st, bad = gpu_lib.sync_status(g, f)
@@ -144,7 +145,7 @@ def test_fp64_rescue_of_ill_conditioned_rows(gpu_lib, k):
     assert np.isfinite(v).all()
     assert rel_norm(v, oracle.generate(fo, want["nbr_pos"], k, 256, xi.astype(np.float64))) < tol
     if k <= 16:
-        vf = np_(gpu_lib.generate_fused(g, gpu_lib.Kernel(*kern), to_gpu(xi)))
+        vf = np_(gpu_lib.generate_fused(g, gpu_lib.Kernel(*kern, rescue_tol=LDR_RESCUE), to_gpu(xi)))
         assert np.array_equal(vf.view(np.uint32), v.view(np.uint32))
     vbar, tb = gpu_lib.nll_backward(g, f, to_gpu(v))
     assert np.isfinite(np_(vbar)).all() and np.isfinite(np_(tb)).all()
@@ -155,7 +156,9 @@ def test_fp64_rescue_of_ill_conditioned_rows(gpu_lib, k):
 @pytest.mark.parametrize("d", [1, 2])
 def test_factor_and_sweeps_lower_dimensions(gpu_lib, d):
     """A 2-D (1-D) cloud: factor, generate and whiten against the oracle on the
-    zero-padded points."""
+    zero-padded points (2-D: 1e-3; 6000 points in the unit square put
+    neighbours at about a quarter of the lengthscale, where the FP32
+    conditionals keep about 2e-4)."""
     N, k = 6000, 8
     pts = workloads.uniform_cube(N, 80 + d)
     pts[:, d:] = 0.0
@@ -164,10 +167,11 @@ def test_factor_and_sweeps_lower_dimensions(gpu_lib, d):
     kern = (1, 1.0, 0.05, 1e-5)
     fo = oracle.factor(want["pts_pos"], want["nbr_pos"], k, 64, oracle.Kernel(*kern))
     f = gpu_lib.factor(g, gpu_lib.Kernel(*kern))
-    _check_factor(gpu_lib, g, f, want, fo, TOL)
+    tol = LDR_TOL if d == 2 else TOL
+    _check_factor(gpu_lib, g, f, want, fo, tol)
     xi = workloads.white_noise(N, 9)
     v = np_(gpu_lib.generate(g, f, to_gpu(xi)))
-    assert rel_norm(v, oracle.generate(fo, want["nbr_pos"], k, 64, xi.astype(np.float64))) < TOL
+    assert rel_norm(v, oracle.generate(fo, want["nbr_pos"], k, 64, xi.astype(np.float64))) < tol
 
 
 @pytest.mark.parametrize("n0", [17, 320, 321, 700])
