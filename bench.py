@@ -124,8 +124,90 @@ def replica_seed(base, rank):
     return base + rank
 
 
-def cpu_baseline(N_sample=1 << 18, reps=10):
-    """The FP64 oracle, as it stands, on a bounded sample of the workload."""
+def _cpu_model():
+    """Host CPU model name and logical core count."""
+    name = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                name = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not name:
+        import platform
+        name = platform.processor() or platform.machine()
+    return name, os.cpu_count() or 1
+
+
+def _oracle_cloud(kind, N, seed):
+    import workloads
+    return {"gaussian": workloads.unit_gaussian, "ldr": workloads.ldr_cloud,
+            "uniform": workloads.uniform_cube}[kind](N, seed)
+
+
+def _oracle_stages(kind, N, k, kern, seed, xi_seed, reps=3):
+    """Seconds of each stage of the FP64 oracle, as it stands, on one thread:
+    graph build (sequential tree search for the k preceding neighbours),
+    factor, generate, whiten, logdet (medians of `reps` passes for the
+    sweeps)."""
+    import numpy as np
+    import oracle
+    import workloads
+    pts = _oracle_cloud(kind, N, seed)
+    t0 = time.perf_counter()
+    g = oracle.build_graph(pts, k, 256, knn="tree")
+    t_graph = time.perf_counter() - t0
+    K = oracle.Kernel(*kern)
+    t0 = time.perf_counter()
+    fo = oracle.factor(g["pts_pos"], g["nbr_pos"], k, g["n0"], K)
+    t_factor = time.perf_counter() - t0
+    xi = workloads.white_noise(N, xi_seed).astype(np.float64)
+    tg, tw, tl = [], [], []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        v = oracle.generate(fo, g["nbr_pos"], k, g["n0"], xi)
+        t1 = time.perf_counter()
+        oracle.whiten(fo, g["nbr_pos"], k, g["n0"], v)
+        t2 = time.perf_counter()
+        oracle.logdet(fo["sigma"])
+        t3 = time.perf_counter()
+        tg.append(t1 - t0)
+        tw.append(t2 - t1)
+        tl.append(t3 - t2)
+    return {"N": N, "k": k, "graph_s": t_graph, "factor_s": t_factor,
+            "generate_s": statistics.median(tg), "whiten_s": statistics.median(tw),
+            "logdet_s": statistics.median(tl)}
+
+
+def _replica_step_rate(args):
+    """One replica of the headline sample on one host core: points/s of
+    generate + whiten + logdet (graph and factor untimed)."""
+    N, seed, reps = args
+    sys.path.insert(0, ROOT)
+    import oracle
+    import workloads
+    w = workloads.WORKLOADS["metric"]
+    pts = workloads.unit_gaussian(N, seed)
+    g = oracle.build_graph(pts, w["k"], 256, knn="tree")
+    fo = oracle.factor(g["pts_pos"], g["nbr_pos"], w["k"], 256, oracle.Kernel(*w["kernel"]))
+    xi = workloads.white_noise(N, w["xi_seed"]).astype("float64")
+    times = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        v = oracle.generate(fo, g["nbr_pos"], w["k"], 256, xi)
+        oracle.whiten(fo, g["nbr_pos"], w["k"], 256, v)
+        oracle.logdet(fo["sigma"])
+        times.append(time.perf_counter() - t0)
+    return N / statistics.median(times)
+
+
+def cpu_baseline(N_sample=1 << 18, reps=10, stages=False):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload:
+    one thread, and (stages=True) every host core running an independent
+    replica, plus the per-stage times of the tiny, large-dynamic-range and
+    headline-sample workloads on one thread."""
     import numpy as np
     import oracle
     import workloads
@@ -147,12 +229,35 @@ def cpu_baseline(N_sample=1 << 18, reps=10):
         oracle.logdet(fo["sigma"])
         times.append(time.perf_counter() - t0)
     t_step = statistics.median(times)
-    return {"value": N_sample / t_step, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": (f"unit-Gaussian cloud of {N_sample} points, k={w['k']}, n0=256, same kernel; "
-                       f"median of {reps} generate+whiten+logdet passes (FP64, 1 thread); "
-                       f"oracle graph build {t_graph:.1f} s and factor {t_factor:.1f} s untimed"),
-            "ms_per_step": t_step * 1e3,
-            "graph_points_per_s": N_sample / t_graph, "factor_points_per_s": N_sample / t_factor}
+    model, ncpu = _cpu_model()
+    out = {"value": N_sample / t_step, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": (f"unit-Gaussian cloud of {N_sample} points, k={w['k']}, n0=256, same kernel; "
+                      f"median of {reps} generate+whiten+logdet passes (FP64, 1 thread of "
+                      f"{ncpu}, {model}); oracle graph build {t_graph:.1f} s and factor "
+                      f"{t_factor:.1f} s untimed"),
+           "ms_per_step": t_step * 1e3, "host_cores": ncpu, "cpu_model": model,
+           "graph_points_per_s": N_sample / t_graph, "factor_points_per_s": N_sample / t_factor}
+    if stages:
+        import multiprocessing as mp
+        ctx = mp.get_context("spawn")
+        n_rep = 1 << 16
+        with ctx.Pool(ncpu) as pool:
+            rates = pool.map(_replica_step_rate, [(n_rep, 100 + r, 5) for r in range(ncpu)])
+        out["all_cores"] = {"value": float(sum(rates)), "unit": UNIT, "cores": ncpu,
+                            "sample": (f"{ncpu} independent replicas of a {n_rep}-point "
+                                       "unit-Gaussian sample, one per host core; generate + "
+                                       "whiten + logdet, median of 5 passes each")}
+        tiny = workloads.WORKLOADS["tiny"]
+        ldr = workloads.WORKLOADS["ldr"]
+        out["stages_1_thread"] = {
+            "tiny": _oracle_stages("uniform", tiny["N"], tiny["k"], tiny["kernel"], tiny["seed"],
+                                   tiny["xi_seed"]),
+            "large_dynamic_range": _oracle_stages("ldr", ldr["N"], ldr["k"], ldr["kernel"],
+                                                  ldr["seed"], ldr["xi_seed"], reps=1),
+            "headline_sample": {"N": N_sample, "k": w["k"], "graph_s": t_graph,
+                                "factor_s": t_factor, "step_s": t_step},
+        }
+    return out
 
 
 def serving_bench(n_inst=64, rate=2000.0, duration=5.0, seed=8, n_slots=8):
@@ -270,6 +375,70 @@ def differentiation_bench(stream, reps=3):
             "nll_and_gradient_ms": ms, "points_per_s": N / (ms / 1e3),
             "point_gradient_ms": pts_ms,
             "factor_ms": t_factor * 1e3, "status": st}
+
+
+def config_leg(name, stream, hbm, reps=5):
+    """Throughput of one configured workload on its own (graph, factor,
+    generate, whiten, logdet), with its sweeps against the HBM roofline:
+    the large-dynamic-range cloud (N = 2^20, k = 16, Matern-3/2 l = 0.05, no
+    nugget, FP64 rescue threshold 2^-10) or the scale cloud (N = 2^29,
+    10^4 blobs + 10 % background, k = 16, Matern-3/2 l = 0.02, nugget 1e-6)."""
+    import torch
+
+    import paper_2606_11402_gb300 as gg
+    import workloads
+    w = workloads.WORKLOADS[name]
+    N, k = w["N"], w["k"]
+    tol = 2.0 ** -10 if name == "ldr" else 0.0
+    kern = gg.Kernel(*w["kernel"], rescue_tol=tol)
+    t0 = time.perf_counter()
+    pts_h = workloads.cloud(w["cloud"], N, w["seed"])
+    t_gen = time.perf_counter() - t0
+    pts = torch.from_numpy(pts_h).cuda()
+    del pts_h
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g = gg.build_graph(pts, k, n0=256)
+    torch.cuda.synchronize()
+    t_graph = time.perf_counter() - t0
+    del pts
+    torch.cuda.empty_cache()
+    t0 = time.perf_counter()
+    f = gg.factor(g, kern)
+    torch.cuda.synchronize()
+    t_factor = time.perf_counter() - t0
+    st, nbad = gg.sync_status(g, f)
+    xi = torch.from_numpy(workloads.white_noise(N, w["xi_seed"])).cuda()
+    v = torch.empty_like(xi)
+    xo = torch.empty_like(xi)
+    ld = torch.empty(1, dtype=torch.float64, device="cuda")
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+    gen_ms = timed(lambda: gg.generate(g, f, xi, out=v))
+    wh_ms = timed(lambda: gg.whiten(g, f, v, out=xo))
+    ld_ms = timed(lambda: gg.logdet(f, out=ld))
+    rt = float(torch.linalg.vector_norm((xo - xi).double()) / torch.linalg.vector_norm(xi.double()))
+    alg = (N - g.n0) * (8 * k + 16)
+    out = {"workload": name, "N": N, "k": k, "levels": g.num_levels, "rescue_tol": tol or 2.0 ** -7,
+           "host_cloud_s": t_gen, "graph_build_s": t_graph, "graph_points_per_s": N / t_graph,
+           "factor_s": t_factor, "factor_points_per_s": N / t_factor, "not_pd_rows": nbad,
+           "generate_ms": gen_ms, "generate_points_per_s": N / (gen_ms / 1e3),
+           "generate_hbm_frac": alg / (gen_ms / 1e3) / 1e9 / hbm,
+           "whiten_ms": wh_ms, "whiten_points_per_s": N / (wh_ms / 1e3),
+           "whiten_hbm_frac": alg / (wh_ms / 1e3) / 1e9 / hbm,
+           "logdet_ms": ld_ms, "whiten_generate_roundtrip_rel": rt, "status": st}
+    del g, f, xi, v, xo
+    torch.cuda.empty_cache()
+    return out
 
 
 def headline_config(N=1 << 26, k=16, n0=256, world=1):
@@ -490,9 +659,20 @@ def run_ours(args):
     for key in list(adj):
         adj[key.replace("_ms", "_points_per_s")] = N / (adj[key] / 1e3)
     diff = differentiation_bench(stream) if args.diff else None
-
     hbm, peak_kind = _peaks()
-    rows = N - g.n0
+    legs = {}
+    if args.legs and not args.N:
+        # the headline instance is released first: the scale leg holds ~150 GB
+        rows_h, levels_h, n0_h = N - g.n0, g.num_levels, g.n0
+        del f, g, v, xo, vbar, xi_d, v_d, xo_d
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        for name in ("ldr", "scale"):
+            legs[name] = config_leg(name, stream, hbm)
+    else:
+        rows_h, levels_h, n0_h = N - g.n0, g.num_levels, g.n0
+
+    rows = rows_h
     bytes_per_point = 8 * k + 16
     alg_bytes = rows * bytes_per_point
     dom = "generate" if gen_ms >= wh_ms else "whiten"
@@ -502,7 +682,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": dict(headline_config(N, k, g.n0, world), levels=g.num_levels),
+        "config": dict(headline_config(N, k, n0_h, world), levels=levels_h),
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm,
                      "unit": "GB/s", "frac": achieved / hbm,
                      "traffic": _measured_traffic(
@@ -528,14 +708,19 @@ def run_ours(args):
     }
     if diff is not None:
         line["differentiation"] = diff
+    if legs:
+        line["configs"] = legs
     if rank == 0 and not args.no_serve:
         sb = serving_bench(duration=args.serve_duration)
         line["serving"] = sb
         line["serving_p50_ms"] = sb["engine"]["p50_ms"]
         line["serving_p99_ms"] = sb["engine"]["p99_ms"]
     if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = {kk: vv for kk, vv in cpu_baseline().items()
+        cb = cpu_baseline(stages=True)
+        line["cpu_baseline"] = {kk: vv for kk, vv in cb.items()
                                 if kk in ("value", "unit", "cores", "kind", "sample")}
+        line["cpu_baseline_detail"] = {kk: cb[kk] for kk in
+                                       ("host_cores", "cpu_model", "all_cores", "stages_1_thread")}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
@@ -556,6 +741,8 @@ def main():
     ap.add_argument("--serve-duration", type=float, default=5.0)
     ap.add_argument("--no-diff", dest="diff", action="store_false",
                     help="skip the differentiation-workload timing")
+    ap.add_argument("--no-legs", dest="legs", action="store_false",
+                    help="skip the large-dynamic-range and scale workload legs")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
