@@ -204,12 +204,15 @@ int graphgp_nll(graphgp_graph_t g, graphgp_factor_t f, const float* v_d,
  * cannot allocate while they run, e.g. a serving loop that reserved all
  * device memory for resident graphs up front, or a latency-critical path that
  * must not pay cudaMalloc's device-wide synchronisation).  The reduction
- * scratch is a 512 KiB array inside the library, one FP64 slot per whiten
- * tile (4096 points) plus one: graphs with N > 2^28 points or more than 8192
- * depth levels are rejected with GRAPHGP_ERR_INVALID.  The array's device
- * address is looked up on the first call made on each device (make that call
- * before any stream capture); the array stays allocated on every device that
- * loaded the library until the process exits.  All calls share it: calls that
+ * scratch is a 514 KiB array inside the library, one FP64 slot per eight
+ * dense rows (up to 256) and one per whiten tile (4096 points): graphs with
+ * N > 2^28 points or more than 8192 depth levels are rejected with
+ * GRAPHGP_ERR_INVALID, before any work and without writing out_d.  The
+ * array's device address is looked up on the first call made on each device
+ * (make that call before any stream capture) and kept for the life of the
+ * process: a cudaDeviceReset on that device voids it, so do not call this
+ * entry point after resetting the device.  The array stays allocated on
+ * every device that loaded the library until the process exits.  All calls share it: calls that
  * overlap on the GPU race, so never run two concurrently on one device.
  * The final sum runs in a fixed order. */
 int graphgp_nll_noalloc(graphgp_graph_t g, graphgp_factor_t f, const float* v_d,
@@ -221,9 +224,10 @@ int graphgp_nll_noalloc(graphgp_graph_t g, graphgp_factor_t f, const float* v_d,
  * the pass from the coordinates and `kern` (same validity rules as
  * graphgp_factor), so no graphgp_factor_t is needed and the device holds the
  * graph alone (about k + 4 words per point instead of 2k + 5).  For kernel
- * parameters that change at every step.  Requires k <= 16, else
- * GRAPHGP_ERR_INVALID.  Results are bit-identical to graphgp_factor followed
- * by the stored-factor sweep (the factor and the dot products run in the same
+ * parameters that change at every step.  Requires k <= 32, else
+ * GRAPHGP_ERR_INVALID (k <= 16: one thread per point; 16 < k <= 32: one warp
+ * per point).  Results are bit-identical to graphgp_factor followed by the
+ * stored-factor sweep (the factor and the dot products run in the same
  * order); the log-determinant equals graphgp_logdet up to the order of its
  * FP64 partial sums.
  *   generate_fused: v_d = L xi_d.

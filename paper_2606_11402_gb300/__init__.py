@@ -315,7 +315,7 @@ def _opt(t, dtype, n, what):
 def generate_fused(graph: Graph, kernel: Kernel, xi: torch.Tensor, out: torch.Tensor | None = None,
                    not_pd: torch.Tensor | None = None, stream=None) -> torch.Tensor:
     """graphgp_generate_fused: v = L xi with the factors recomputed in the pass
-    (k <= 16); not_pd (int64[1], optional) has the floored pivots added."""
+    (k <= 32); not_pd (int64[1], optional) has the floored pivots added."""
     v = torch.empty_like(xi) if out is None else out
     kc = kernel._c()
     _check(load().graphgp_generate_fused(graph.handle, ctypes.byref(kc),

@@ -332,6 +332,11 @@ inline unsigned grid_for(int64_t n, int block, int64_t cap_per_sm = 32) {
 int radix_sort_pairs(const uint32_t* keys_in, const uint32_t* vals_in,
                      uint32_t* keys_out, uint32_t* vals_out, int64_t n,
                      int bits, cudaStream_t s);
+// on-the-fly sweeps of the 32-lane group form (16 < k <= 32), fused_group.cu
+int whiten_fused_group(graphgp_graph_t g, int type, const KernF& kf, const float* v, float* xi,
+                       double* sq, double* logdet, unsigned long long* not_pd, cudaStream_t s);
+int generate_fused_group(graphgp_graph_t g, int type, const KernF& kf, const float* xi, float* v,
+                         unsigned long long* not_pd, cudaStream_t s);
 // exclusive scan of uint32 counts into uint32 offsets; returns total on request
 int scan_exclusive_u32(const uint32_t* in, uint32_t* out, int64_t n,
                        cudaStream_t s);

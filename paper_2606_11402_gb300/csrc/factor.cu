@@ -45,6 +45,9 @@ __global__ void __launch_bounds__(128) point_factor_kernel(
   constexpr int PPW = 32 / G;  // points per warp
   constexpr int GS = PFLayout<G>::GS;
   __shared__ __align__(16) float Ls[4 * PPW * GS];
+  // FP64 rescue workspace of each warp (dynamic: 4 G (G + 1) doubles)
+  extern __shared__ __align__(16) double gwsm[];
+  double* Wwarp = gwsm + (threadIdx.x >> 5) * (G * (G + 1));
   const int lane = threadIdx.x & 31;
   const int grp = lane / G;
   const int a = lane % G;
@@ -69,20 +72,22 @@ __global__ void __launch_bounds__(128) point_factor_kernel(
     const bool lane_bad = a < k && !isfinite(st.b_own);
     const bool rescue = st.clamped || row_error_too_large(st.max_ratio, st.varw, st.sigma, kf) ||
                         !isfinite(st.sigma) || (__ballot_sync(0xffffffffu, lane_bad) & gmask);
+    static_assert(G == 32, "the group factor kernel runs one point per warp");
     bool deferred = false;
     if (valid && rescue && a == 0) deferred = rl.defer(i);
-    deferred = __shfl_sync(0xffffffffu, deferred, grp * G);
+    deferred = __shfl_sync(0xffffffffu, deferred, 0);
+    if (valid && rescue && !deferred) {  // list full: the warp recomputes the row in place
+      const WarpRow64 w = warp_row_factor64<G, KT>(xs, nbr + (i - n0) * kp, k, xs[i], kf, Wwarp);
+      if (a < kp) b_out[(i - n0) * kp + a] = a < k ? (float)w.b : 0.0f;
+      if (a == 0) {
+        const float sg = (float)w.sigma;
+        sigma_out[i] = sg;
+        acc.mul(sg);
+        if (w.clamped) clamped_rows++;
+      }
+    }
     if (valid && !deferred) {
       if (rescue) {
-        if (a == 0) {
-          Row64<G> R;
-          row_factor64<G, KT>(R, xs, nbr + (i - n0) * kp, k, xs[i], kf);
-          for (int e = 0; e < kp; e++) b_out[(i - n0) * kp + e] = e < k ? (float)R.b[e] : 0.0f;
-          const float sg = (float)R.sigma;
-          sigma_out[i] = sg;
-          acc.mul(sg);
-          if (R.clamped) clamped_rows++;
-        }
       } else {
         if (a < kp) b_out[(i - n0) * kp + a] = a < k ? st.b_own : 0.0f;
         if (a == 0) {
@@ -110,20 +115,31 @@ __global__ void __launch_bounds__(128) point_factor_thread_kernel(
     double* __restrict__ logdet, unsigned long long* __restrict__ not_pd, RescueList rl) {
   extern __shared__ __align__(16) unsigned char tstage[];
   const ThreadStage<K> st(tstage);
+  double* W = reinterpret_cast<double*>(tstage + ThreadStage<K>::kBytes) +
+              (threadIdx.x >> 5) * (warp_rescue_bytes<K>() / sizeof(double));
   LogAcc acc;
   unsigned long long clamped_rows = 0;
   const int64_t npts = N - n0;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < npts;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = n0 + t;
-    stage_coords<K>(st, xs, nbr + t * K, k);
+  const int64_t total = (int64_t)gridDim.x * blockDim.x;
+  const int64_t iters = (npts + total - 1) / total;  // the same on every lane
+  for (int64_t it = 0; it < iters; it++) {
+    const int64_t t = it * total + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const bool valid = t < npts;
+    const int64_t i = n0 + (valid ? t : 0);
+    const int32_t* row = nbr + (valid ? t : 0) * K;
     PointRegs<K> p;
     const float4 xq = __ldg(xs + i);
-    point_factor_thread<K, KT>(p, k, kf, st, xq);
-    if (needs_rescue(p, k, kf)) {
-      if (rl.defer(i)) continue;
-      rescue_thread<K, KT>(p, xs, nbr + t * K, k, xq, kf);
+    bool deferred = false, rescue = false;
+    if (valid) {
+      stage_coords<K>(st, xs, row, k);
+      point_factor_thread<K, KT>(p, k, kf, st, xq);
+      if (needs_rescue(p, k, kf)) {
+        deferred = rl.defer(i);
+        rescue = !deferred;
+      }
     }
+    warp_rescue<K, KT>(p, rescue, xs, row, k, xq, kf, W);  // list full: in place
+    if (!valid || deferred) continue;
     float4* bo = reinterpret_cast<float4*>(b_out + t * K);
 #pragma unroll
     for (int q = 0; q < K / 4; q++)
@@ -189,6 +205,38 @@ __global__ void __launch_bounds__(128) point_factor_wide_kernel(
 
 // The FP64 rows listed by the factor kernels: b (row stride kp), sigma, and
 // their log-determinant and floor counts.
+// k <= 32: one warp per listed row (warp_row_factor64, the routine of every
+// other rescue of these k).
+template <int KMAX, int KT>
+__global__ void __launch_bounds__(128) factor_rescue_warp_kernel(
+    const float4* __restrict__ xs, const int32_t* __restrict__ nbr, int k, int kp, int64_t n0,
+    KernF kf, RescueList rl, float* __restrict__ b_out, float* __restrict__ sigma_out,
+    double* __restrict__ logdet, unsigned long long* __restrict__ not_pd) {
+  __shared__ double Wsm[4][KMAX * (KMAX + 1)];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  LogAcc acc;
+  unsigned long long clamped_rows = 0;
+  const unsigned long long cnt = *rl.count;
+  const int64_t n = (int64_t)(cnt < rl.cap ? cnt : rl.cap);
+  for (int64_t r = blockIdx.x * 4 + warp; r < n; r += (int64_t)gridDim.x * 4) {
+    const int64_t i = rl.rows[r];
+    const int64_t t = i - n0;
+    const WarpRow64 w = warp_row_factor64<KMAX, KT>(xs, nbr + t * kp, k, __ldg(xs + i), kf,
+                                                    Wsm[warp]);
+    if (lane < kp) b_out[t * kp + lane] = lane < k ? (float)w.b : 0.0f;
+    if (lane == 0) {
+      const float sg = (float)w.sigma;
+      sigma_out[i] = sg;
+      acc.mul(sg);
+      if (w.clamped) clamped_rows++;
+    }
+  }
+  block_add_double(lane == 0 ? acc.log_value() : 0.0, logdet);
+  for (int o = 16; o; o >>= 1) clamped_rows += __shfl_xor_sync(0xffffffffu, clamped_rows, o);
+  if (lane == 0 && clamped_rows) atomicAdd(not_pd, clamped_rows);
+}
+
+// k > 32: one thread per listed row.
 template <int KMAX, int KT>
 __global__ void __launch_bounds__(128) factor_rescue_kernel(
     const float4* __restrict__ xs, const int32_t* __restrict__ nbr, int k, int kp, int64_t n0,
@@ -220,8 +268,13 @@ int launch_rescue(int type, graphgp_graph_t g, graphgp_factor_t f, const KernF& 
                   const RescueList& rl, cudaStream_t s) {
   const unsigned grid = 4 * (unsigned)num_sms();
 #define GGP_RS(KT)                                                                          \
-  factor_rescue_kernel<KMAX, KT><<<grid, 128, 0, s>>>(g->xs, g->nbr, g->k, g->kp, g->n0, kf, \
-                                                      rl, f->b, f->sigma, f->logdet, f->not_pd)
+  if constexpr (KMAX <= 32) {                                                               \
+    factor_rescue_warp_kernel<KMAX, KT><<<grid, 128, 0, s>>>(                               \
+        g->xs, g->nbr, g->k, g->kp, g->n0, kf, rl, f->b, f->sigma, f->logdet, f->not_pd);   \
+  } else {                                                                                  \
+    factor_rescue_kernel<KMAX, KT><<<grid, 128, 0, s>>>(                                    \
+        g->xs, g->nbr, g->k, g->kp, g->n0, kf, rl, f->b, f->sigma, f->logdet, f->not_pd);   \
+  }
   switch (type) {
     case GRAPHGP_MATERN12: GGP_RS(GRAPHGP_MATERN12); break;
     case GRAPHGP_MATERN32: GGP_RS(GRAPHGP_MATERN32); break;
@@ -513,9 +566,13 @@ int launch_point(int type, graphgp_graph_t g, graphgp_factor_t f, const KernF& k
   constexpr int PPW = 32 / G;
   int64_t groups_per_block = 4 * PPW;
   unsigned grid = grid_for((npts + groups_per_block - 1) / groups_per_block * 128, 128, 16);
+  constexpr size_t smem = 4 * (size_t)G * (G + 1) * sizeof(double);
 #define GGP_PF(KT)                                                                       \
-  point_factor_kernel<G, KT><<<grid, 128, 0, s>>>(g->xs, g->nbr, g->N, g->k, g->kp, g->n0, \
-                                                  kf, f->b, f->sigma, f->logdet, f->not_pd, rl)
+  GGP_CUDA(cudaFuncSetAttribute(point_factor_kernel<G, KT>,                              \
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
+  point_factor_kernel<G, KT><<<grid, 128, smem, s>>>(g->xs, g->nbr, g->N, g->k, g->kp,   \
+                                                     g->n0, kf, f->b, f->sigma, f->logdet, \
+                                                     f->not_pd, rl)
   switch (type) {
     case GRAPHGP_MATERN12: GGP_PF(GRAPHGP_MATERN12); break;
     case GRAPHGP_MATERN32: GGP_PF(GRAPHGP_MATERN32); break;
@@ -532,7 +589,7 @@ int launch_point_thread(int type, graphgp_graph_t g, graphgp_factor_t f, const K
                         const RescueList& rl, cudaStream_t s) {
   const int64_t npts = g->N - g->n0;
   const unsigned grid = grid_for(npts, kThreadBlock, 8);
-  constexpr size_t smem = ThreadStage<K>::kBytes;
+  constexpr size_t smem = ThreadStage<K>::kBytes + 4 * warp_rescue_bytes<K>();
 #define GGP_PT(KT)                                                                            \
   GGP_CUDA(allow_dyn_smem(point_factor_thread_kernel<K, KT>, smem));                          \
   point_factor_thread_kernel<K, KT><<<grid, kThreadBlock, smem, s>>>(                         \

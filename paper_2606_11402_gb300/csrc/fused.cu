@@ -5,9 +5,9 @@
 // of 2k + 5 with stored weights); this is the form for kernel parameters that
 // change at every step.
 //
-// Each thread owns one point and runs point_factor_thread (k <= 16) with the
-// same FP64 rescue decision as the factor kernel, so b and sigma are
-// bit-identical to the stored factor's; the dot b . v_c then
+// Each thread owns one point and runs point_factor_thread (k <= 16; 16 < k
+// <= 32 in fused_group.cu) with the same FP64 rescue decision as the factor
+// kernel, so b and sigma are bit-identical to the stored factor's; the dot b . v_c then
 // follows the stored sweeps' summation order (the row cut into gen_lanes(K)
 // slices, two alternating accumulators per slice, slices combined as their
 // xor-shuffle tree does), so the fused sweeps return the same bits as
@@ -64,7 +64,17 @@ __device__ __forceinline__ void factor_at(PointRegs<K>& p, const ThreadStage<K>&
   const float4 xq = __ldg(xs + i);
   stage_coords<K>(st, xs, row, k);
   point_factor_thread<K, KT>(p, k, kf, st, xq);
-  if (needs_rescue(p, k, kf)) rescue_thread<K, KT>(p, xs, row, k, xq, kf);
+}
+
+// Dynamic shared memory of the one-thread-per-point fused kernels: the
+// staging area, then each warp's FP64 rescue workspace.
+template <int K>
+constexpr size_t fused_smem() { return ThreadStage<K>::kBytes + 4 * warp_rescue_bytes<K>(); }
+
+template <int K>
+__device__ __forceinline__ double* fused_rescue_ws(unsigned char* smem) {
+  return reinterpret_cast<double*>(smem + ThreadStage<K>::kBytes) +
+         (threadIdx.x >> 5) * (warp_rescue_bytes<K>() / sizeof(double));
 }
 
 __device__ inline void block_add_count(unsigned long long c, unsigned long long* out) {
@@ -79,17 +89,23 @@ __global__ void __launch_bounds__(128) whiten_fused_kernel(
     double* __restrict__ logdet, unsigned long long* __restrict__ not_pd) {
   extern __shared__ __align__(16) unsigned char tstage[];
   const ThreadStage<K> stg(tstage);
+  double* W = fused_rescue_ws<K>(tstage);
   const uint64_t pol_v = l2_evict_last();
   LogAcc lacc;
   double local = 0.0;
   unsigned long long clamped = 0;
   const int64_t npts = N - n0;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < npts;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = n0 + t;
-    const int32_t* row = nbr + t * K;
+  const int64_t total = (int64_t)gridDim.x * blockDim.x;
+  const int64_t iters = (npts + total - 1) / total;  // the same on every lane
+  for (int64_t it = 0; it < iters; it++) {
+    const int64_t t = it * total + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const bool valid = t < npts;
+    const int64_t i = n0 + (valid ? t : 0);
+    const int32_t* row = nbr + (valid ? t : 0) * K;
     PointRegs<K> p;
-    factor_at<K, KT>(p, stg, xs, row, i, k, kf);
+    if (valid) factor_at<K, KT>(p, stg, xs, row, i, k, kf);
+    warp_rescue<K, KT>(p, valid && needs_rescue(p, k, kf), xs, row, k, __ldg(xs + i), kf, W);
+    if (!valid) continue;
     const float acc = dot_stored_order<K, false>(p.y, row, v, pol_v);
     const float out = (ld_keep_f(v + i, pol_v) - acc) / p.sigma;
     xi[i] = out;
@@ -110,6 +126,7 @@ __global__ void __launch_bounds__(128) generate_fused_kernel(
   __shared__ int s_flag;
   extern __shared__ __align__(16) unsigned char tstage[];
   const ThreadStage<K> stg(tstage);
+  double* W = fused_rescue_ws<K>(tstage);
   const uint64_t pol_v = l2_evict_last();
   unsigned long long clamped = 0;
   for (int l = 1; l < num_levels; l++) {
@@ -125,6 +142,8 @@ __global__ void __launch_bounds__(128) generate_fused_kernel(
       const int32_t* row = nbr + (active ? q - n0 : 0) * K;
       PointRegs<K> p;
       if (active) factor_at<K, KT>(p, stg, xs, row, q, k, kf);
+      warp_rescue<K, KT>(p, active && needs_rescue(p, k, kf), xs, row, k,
+                         __ldg(xs + (active ? q : n0)), kf, W);
       // the level's inputs are complete once every block arrived at l - 1
       if (st == 0 && l > 1 && lb.wait(l - 1, gridDim.x, &s_flag)) return;
       if (active) {
@@ -172,7 +191,7 @@ int launch_whiten_fused(graphgp_graph_t g, int type, const KernF& kf, const floa
   const int64_t npts = g->N - g->n0;
   if (npts <= 0) return GRAPHGP_OK;
   const unsigned grid = grid_for(npts, kThreadBlock, 8);
-  constexpr size_t smem = ThreadStage<K>::kBytes;
+  constexpr size_t smem = fused_smem<K>();
 #define GGP_WF(KT)                                                                            \
   GGP_CUDA(allow_dyn_smem(whiten_fused_kernel<K, KT>, smem));                                 \
   whiten_fused_kernel<K, KT><<<grid, kThreadBlock, smem, s>>>(g->xs, g->nbr, g->N, g->k, g->n0, \
@@ -191,7 +210,7 @@ int launch_whiten_fused(graphgp_graph_t g, int type, const KernF& kf, const floa
 template <int K, int KT>
 int launch_generate_fused_kt(graphgp_graph_t g, const KernF& kf, const float* xi, float* v,
                              unsigned long long* not_pd, cudaStream_t s) {
-  constexpr size_t smem = ThreadStage<K>::kBytes;
+  constexpr size_t smem = fused_smem<K>();
   GGP_CUDA(allow_dyn_smem(generate_fused_kernel<K, KT>, smem));
   static int max_grid_dev[kMaxDevices] = {};
   const int max_grid = coop_grid_cached(max_grid_dev, generate_fused_kernel<K, KT>, kThreadBlock, smem);
@@ -240,6 +259,7 @@ int whiten_fused(graphgp_graph_t g, const graphgp_kernel* kern, const float* v, 
   if (rc == GRAPHGP_OK) rc = dense_matvec(f.L0inv, v, xi, g->n0, sq, s);
   if (rc == GRAPHGP_OK) {
     const KernF kf = make_kernf(*kern);
+    if (g->kp > 16) return whiten_fused_group(g, kern->type, kf, v, xi, sq, logdet, not_pd, s);
 #define GGP_CALL(K) rc = launch_whiten_fused<K>(g, kern->type, kf, v, xi, sq, logdet, not_pd, s)
     GGP_FUSED_DISPATCH(GGP_CALL)
 #undef GGP_CALL
@@ -253,7 +273,7 @@ int whiten_fused(graphgp_graph_t g, const graphgp_kernel* kern, const float* v, 
 using namespace ggp;
 
 static bool fused_ok(graphgp_graph_t g, const graphgp_kernel* kern) {
-  return g && valid_kernel(kern) && g->kp <= 16;
+  return g && valid_kernel(kern) && g->k <= 32;
 }
 
 extern "C" int graphgp_generate_fused(graphgp_graph_t g, const graphgp_kernel* kern,
@@ -275,6 +295,7 @@ extern "C" int graphgp_generate_fused(graphgp_graph_t g, const graphgp_kernel* k
   if (rc == GRAPHGP_OK) rc = dense_matvec(f.L0, xi_d, v_d, g->n0, nullptr, s);
   if (rc == GRAPHGP_OK) {
     const KernF kf = make_kernf(*kern);
+    if (g->kp > 16) return generate_fused_group(g, kern->type, kf, xi_d, v_d, bad, s);
 #define GGP_CALL(K) rc = launch_generate_fused<K>(g, kern->type, kf, xi_d, v_d, bad, s)
     GGP_FUSED_DISPATCH(GGP_CALL)
 #undef GGP_CALL

@@ -7,9 +7,10 @@
 // graphs and factors up front, or code that must not pay cudaMalloc's
 // device-wide synchronisation on a latency-critical path.  This variant keeps
 // its reduction scratch in a file-scope device array instead: one FP64 slot
-// per whiten tile plus one for the dense block.  Every slot is written before
-// it is read, so nothing needs clearing, and the final sum runs in a fixed
-// order (the result does not depend on block scheduling).
+// per block of eight dense rows (up to 256) and one per whiten tile.  Every
+// slot that is summed is written first in the same call, so nothing needs
+// clearing, and the final sum runs in a fixed order (the result does not
+// depend on block scheduling).
 //
 // The array is loaded with the library and held by every GPU that loads it
 // until the process exits.  Its device address is looked up once per device
@@ -22,9 +23,11 @@
 
 #include "sweepsync.cuh"
 
-// One slot per whiten tile (at most 65536 tiles of 4096 points, i.e.
-// N <= 2^28) plus one for the dense block: 512 KiB.
-static constexpr int kNllSlots = 65536 + 1;
+// Up to 256 slots for the dense block (eight rows each, n0 <= 2048) and one
+// per whiten tile (at most 65536 tiles of 4096 points, i.e. N <= 2^28):
+// 514 KiB.
+static constexpr int kDenseSlots = 256;
+static constexpr int kNllSlots = kDenseSlots + 65536;
 static __device__ __align__(256) double g_nll_scratch[kNllSlots];
 
 namespace ggp {
@@ -67,13 +70,13 @@ __device__ double block_sum_fixed(double x) {
   return r;
 }
 
-// Dense block: slot[0] = sum_i (L0^-1 v_0)_i^2, one block of 256 threads,
-// one warp per row.
+// Dense block: slot[b] = sum over rows 8b..8b+7 of (L0^-1 v_0)_i^2; block b
+// of 256 threads, one warp per row.
 __global__ void nll_dense_slot_kernel(const float* __restrict__ W, const float* __restrict__ v,
                                       int n0, double* __restrict__ slot) {
   int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   double local = 0.0;
-  for (int i = w; i < n0; i += blockDim.x >> 5) {
+  for (int i = blockIdx.x * 8 + w; i < n0 && i < (int)(blockIdx.x + 1) * 8; i += 8) {
     const float* r = W + (int64_t)i * n0;
     float s = 0.0f;
     for (int m = lane; m <= i; m += 32) s = fmaf(r[m], v[m], s);
@@ -81,10 +84,10 @@ __global__ void nll_dense_slot_kernel(const float* __restrict__ W, const float* 
     if (lane == 0) local += (double)s * (double)s;
   }
   double t = block_sum_fixed(local);
-  if (threadIdx.x == 0) slot[0] = t;
+  if (threadIdx.x == 0) slot[blockIdx.x] = t;
 }
 
-// One tile per block iteration: slot[1 + t] = sum over the tile's positions of
+// One tile per block iteration: slot[t] = sum over the tile's positions of
 // xi_i^2, xi_i = (v_i - b_i . v_c(i)) / sigma_i.
 template <int KP>
 __global__ void __launch_bounds__(256) nll_tiles_slot_kernel(
@@ -175,16 +178,18 @@ __global__ void __launch_bounds__(256) nll_tiles_slot_kernel(
       }
     }
     double tsum = block_sum_fixed(local);
-    if (threadIdx.x == 0) slot[1 + t] = tsum;
+    if (threadIdx.x == 0) slot[t] = tsum;
   }
 }
 
-// out = 0.5 sum(slots) + 0.5 logdet, summed in a fixed order.
-__global__ void nll_noalloc_finish_kernel(const double* __restrict__ slot, int64_t count,
+// out = 0.5 (sum of the nd dense slots and the nt tile slots) + 0.5 logdet,
+// summed in a fixed order.
+__global__ void nll_noalloc_finish_kernel(const double* __restrict__ slot, int nd, int64_t nt,
                                           const double* __restrict__ logdet,
                                           double* __restrict__ out) {
   double local = 0.0;
-  for (int64_t i = threadIdx.x; i < count; i += blockDim.x) local += slot[i];
+  for (int i = threadIdx.x; i < nd; i += blockDim.x) local += slot[i];
+  for (int64_t i = threadIdx.x; i < nt; i += blockDim.x) local += slot[kDenseSlots + i];
   double t = block_sum_fixed(local);
   if (threadIdx.x == 0) out[0] = 0.5 * t + 0.5 * logdet[0];
 }
@@ -217,35 +222,37 @@ extern "C" int graphgp_nll_noalloc(graphgp_graph_t g, graphgp_factor_t f, const 
                          "supported without allocation\n", g->num_levels);
     return GRAPHGP_ERR_INVALID;
   }
-  int64_t slots = (g->N > g->n0 ? g->n_tiles : 0) + 1;
-  if (slots > kNllSlots) {
-    std::fprintf(stderr, "graphgp_nll_noalloc: N=%lld needs %lld scratch slots; the static "
+  const int64_t nt = g->N > g->n0 ? g->n_tiles : 0;
+  const int nd = (g->n0 + 7) / 8;
+  if (nt > kNllSlots - kDenseSlots || nd > kDenseSlots) {
+    std::fprintf(stderr, "graphgp_nll_noalloc: N=%lld needs %lld tile slots; the static "
                          "scratch holds %d (N <= 2^28)\n",
-                 (long long)g->N, (long long)slots, kNllSlots);
+                 (long long)g->N, (long long)nt, kNllSlots - kDenseSlots);
     return GRAPHGP_ERR_INVALID;
   }
   cudaStream_t s = (cudaStream_t)stream;
   double* slot = nullptr;
   GGP_TRY(nll_scratch(&slot));
-  nll_dense_slot_kernel<<<1, 256, 0, s>>>(f->L0inv, v_d, g->n0, slot);
+  nll_dense_slot_kernel<<<nd, 256, 0, s>>>(f->L0inv, v_d, g->n0, slot);
   GGP_CUDA(cudaGetLastError());
-  if (g->N > g->n0) {
+  if (nt > 0) {
     int rc = GRAPHGP_OK;
+    double* tslot = slot + kDenseSlots;
     switch (g->kp) {
-      case 4: rc = launch_tiles<4>(g, f, v_d, slot, s); break;
-      case 8: rc = launch_tiles<8>(g, f, v_d, slot, s); break;
-      case 12: rc = launch_tiles<12>(g, f, v_d, slot, s); break;
-      case 16: rc = launch_tiles<16>(g, f, v_d, slot, s); break;
-      case 20: rc = launch_tiles<20>(g, f, v_d, slot, s); break;
-      case 24: rc = launch_tiles<24>(g, f, v_d, slot, s); break;
-      case 28: rc = launch_tiles<28>(g, f, v_d, slot, s); break;
-      case 32: rc = launch_tiles<32>(g, f, v_d, slot, s); break;
-      case 48: rc = launch_tiles<48>(g, f, v_d, slot, s); break;
-      default: rc = launch_tiles<64>(g, f, v_d, slot, s); break;
+      case 4: rc = launch_tiles<4>(g, f, v_d, tslot, s); break;
+      case 8: rc = launch_tiles<8>(g, f, v_d, tslot, s); break;
+      case 12: rc = launch_tiles<12>(g, f, v_d, tslot, s); break;
+      case 16: rc = launch_tiles<16>(g, f, v_d, tslot, s); break;
+      case 20: rc = launch_tiles<20>(g, f, v_d, tslot, s); break;
+      case 24: rc = launch_tiles<24>(g, f, v_d, tslot, s); break;
+      case 28: rc = launch_tiles<28>(g, f, v_d, tslot, s); break;
+      case 32: rc = launch_tiles<32>(g, f, v_d, tslot, s); break;
+      case 48: rc = launch_tiles<48>(g, f, v_d, tslot, s); break;
+      default: rc = launch_tiles<64>(g, f, v_d, tslot, s); break;
     }
     if (rc < 0) return rc;
   }
-  nll_noalloc_finish_kernel<<<1, 256, 0, s>>>(slot, slots, f->logdet, out_d);
+  nll_noalloc_finish_kernel<<<1, 256, 0, s>>>(slot, nd, nt, f->logdet, out_d);
   GGP_CUDA(cudaGetLastError());
   return GRAPHGP_OK;
 }

@@ -495,6 +495,47 @@ __device__ __forceinline__ bool needs_rescue(const PointRegs<K>& p, int k, const
   return bad;
 }
 
+// Shared memory of the warp-cooperative FP64 rescue (rescue.cuh) for one warp
+// of a one-thread-per-point kernel: K (K + 1) doubles.
+template <int K>
+__host__ __device__ constexpr size_t warp_rescue_bytes() { return (size_t)K * (K + 1) * sizeof(double); }
+
+// The rows of the warp's lanes with `need` set are recomputed in FP64, one
+// row at a time by the whole warp (warp_row_factor64); each such lane
+// receives its b (zero past k), sigma and floor flag, rounded to FP32.  Every
+// lane of the warp must call this (a collective); W is the warp's shared
+// memory of warp_rescue_bytes<K>().
+template <int K, int KT>
+__device__ __forceinline__ void warp_rescue(PointRegs<K>& p, bool need,
+                                            const float4* __restrict__ xs, const int32_t* row,
+                                            int k, float4 xq, const KernF& kf, double* W) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  unsigned m = __ballot_sync(full, need);
+  while (m) {
+    const int src = __ffs(m) - 1;
+    m &= m - 1;
+    const int32_t* r = reinterpret_cast<const int32_t*>(
+        __shfl_sync(full, reinterpret_cast<unsigned long long>(row), src));
+    float4 q;
+    q.x = __shfl_sync(full, xq.x, src);
+    q.y = __shfl_sync(full, xq.y, src);
+    q.z = __shfl_sync(full, xq.z, src);
+    q.w = 0.0f;
+    const WarpRow64 w = warp_row_factor64<K, KT>(xs, r, k, q, kf, W);
+    float* bf = reinterpret_cast<float*>(W);
+    bf[lane] = (float)w.b;
+    __syncwarp();
+    if (lane == src) {
+#pragma unroll
+      for (int a = 0; a < K; a++) p.y[a] = a < k ? bf[a] : 0.0f;
+      p.sigma = (float)w.sigma;
+      p.clamped = w.clamped;
+    }
+    __syncwarp();
+  }
+}
+
 // The FP64 conditional of the row in place of the FP32 one: b (zero past k),
 // sigma and the floor flag, rounded to FP32.
 template <int K, int KT>

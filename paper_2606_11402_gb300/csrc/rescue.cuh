@@ -124,6 +124,90 @@ __device__ __noinline__ void row_factor64(Row64<KMAX>& R, const float4* __restri
   }
 }
 
+// The FP64 conditional of one row computed by a whole warp (k <= KMAX <= 32):
+// lane a owns neighbour a and row a of K_cc in shared memory (W: KMAX x
+// (KMAX + 1) doubles per warp).  Lane a evaluates its row of kernel values (FP64 distances from the
+// FP32 coordinates), then a right-looking Cholesky by columns with the pivot
+// floor of row_factor64 (1e-7 of the diagonal), the forward solve riding
+// along and sigma^2 = K_ii - y.y summed in column order, and the backward
+// solve b = L^-T y.  A single thread needs k(k+1)/2 FP64 exponentials and
+// k^3/6 dependent FP64 multiply-adds for a row, at the low FP64 rate of this
+// GPU; the warp spreads both over its lanes.  Every path that rescues a row
+// with k <= 32 (factor, on-the-fly sweeps) uses this routine, so stored and
+// recomputed factors agree bit for bit.  All 32 lanes must call it with the
+// same arguments; lane a receives b_a (0 for a >= k).
+struct WarpRow64 {
+  double b;       // this lane's weight
+  double sigma;   // same on every lane
+  bool clamped;   // same on every lane
+};
+
+template <int KMAX, int KT>
+__device__ __noinline__ WarpRow64 warp_row_factor64(const float4* __restrict__ xs,
+                                                    const int32_t* row, int k, float4 xq,
+                                                    const KernF& p, double* W) {
+  static_assert(KMAX <= 32, "one lane per neighbour");
+  constexpr int LD = KMAX + 1;
+  const unsigned full = 0xffffffffu;
+  const int a = threadIdx.x & 31;
+  const bool real = a < k;
+  const double k0 = kappa64<KT>(p, 0.0) + p.nugd;
+  const float4 xa = real ? __ldg(xs + row[a]) : make_float4(0.f, 0.f, 0.f, 0.f);
+  double* La = W + a * LD;
+  for (int c = 0; c < k; c++) {
+    float4 xc;
+    xc.x = __shfl_sync(full, xa.x, c);
+    xc.y = __shfl_sync(full, xa.y, c);
+    xc.z = __shfl_sync(full, xa.z, c);
+    if (real && c < a) La[c] = kappa64<KT>(p, dist64(xa, xc));
+  }
+  double y = real ? kappa64<KT>(p, dist64(xa, xq)) : 0.0;
+  if (real) La[a] = k0;
+  __syncwarp();
+  const double fl = kPdFloor64 * k0;
+  bool clamped = false;
+  double s2 = k0;
+  for (int j = 0; j < k; j++) {
+    double piv = __shfl_sync(full, a == j ? La[j] : 0.0, j);
+    if (!(piv > fl)) {
+      piv = fl;
+      clamped = true;
+    }
+    const double ljj = sqrt(piv);
+    const double yj = __shfl_sync(full, y, j) / ljj;
+    s2 -= yj * yj;
+    double laj = 0.0;
+    if (real && a > j) {
+      laj = La[j] / ljj;
+      La[j] = laj;
+      y -= laj * yj;
+    }
+    if (a == j) {
+      La[j] = ljj;
+      y = yj;
+    }
+    __syncwarp();
+    // trailing update of row a: L_ac -= L_aj L_cj for j < c <= a
+    if (real && a > j)
+      for (int c = j + 1; c <= a; c++) La[c] -= laj * W[c * LD + j];
+    __syncwarp();
+  }
+  if (!(s2 > fl)) {
+    s2 = fl;
+    clamped = true;
+  }
+  // b = L^-T y, last entry first
+  double d = y;
+  double b = 0.0;
+  for (int j = k - 1; j >= 0; j--) {
+    const double bj = __shfl_sync(full, a == j ? d / La[j] : 0.0, j);
+    if (a == j) b = bj;
+    if (real && a < j) d -= W[j * LD + a] * bj;
+  }
+  __syncwarp();
+  return WarpRow64{real ? b : 0.0, sqrt(s2), clamped};
+}
+
 // The row's contribution to thetabar = (d/dl, d/dsigma2, d/dnugget) from the
 // cotangents of its weights, bbar_a = alpha v_c(a), and of its conditional
 // standard deviation, sigbar (Sec. 2.3; with s = sigma^2, g = K_cc^-1 bbar:

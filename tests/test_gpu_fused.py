@@ -17,9 +17,11 @@ def _bits(t):
     return np_(t).view(np.uint32)
 
 
-@pytest.mark.parametrize("k", [1, 5, 8, 12, 16])
+@pytest.mark.parametrize("k", [1, 5, 8, 12, 16, 17, 23, 24, 28, 32])
 @pytest.mark.parametrize("kern", KERNS)
 def test_fused_equals_stored_bitwise(gpu_lib, k, kern):
+    """k <= 16: one thread per point; 16 < k <= 32: one warp per point (every
+    padded row length 20, 24, 28, 32)."""
     N = 20_011
     pts = workloads.cloud("gaussian", N, 90 + k)
     g = gpu_lib.build_graph(to_gpu(pts), k, n0=max(k, 64))
@@ -82,6 +84,27 @@ def test_fused_counts_floored_pivots_and_rejects_large_k(gpu_lib):
     bad = torch.zeros(1, dtype=torch.int64, device="cuda")
     gpu_lib.whiten_fused(g, K, to_gpu(workloads.white_noise(2000, 1)), not_pd=bad)
     assert bad_stored > 0 and int(bad.item()) == bad_stored
-    g32 = gpu_lib.build_graph(to_gpu(base), 17, n0=64)
+    g33 = gpu_lib.build_graph(to_gpu(base), 33, n0=64)
     with pytest.raises(gpu_lib.GraphGPError):
-        gpu_lib.generate_fused(g32, K, to_gpu(workloads.white_noise(1000, 2)))
+        gpu_lib.generate_fused(g33, K, to_gpu(workloads.white_noise(1000, 2)))
+
+
+def test_fused_differentiation_kernel_k32(gpu_lib):
+    """The differentiation workload's kernel (SE, l = 0.03, nugget 1e-4,
+    k = 32) through the on-the-fly sweeps: bit-identical to the stored path
+    and within 1e-4 of the oracle."""
+    N, k, kern = 4096, 32, (3, 1.0, 0.03, 1e-4)
+    pts = workloads.uniform_cube(N, 4)
+    want = oracle.build_graph(pts, k)
+    g = gpu_lib.build_graph(to_gpu(pts), k, n0=want["n0"])
+    K = gpu_lib.Kernel(*kern)
+    f = gpu_lib.factor(g, K)
+    xi = to_gpu(workloads.white_noise(N, 5))
+    vf = gpu_lib.generate_fused(g, K, xi)
+    assert np.array_equal(_bits(vf), _bits(gpu_lib.generate(g, f, xi)))
+    fo = oracle.factor(want["pts_pos"], want["nbr_pos"], k, want["n0"], oracle.Kernel(*kern))
+    v_or = oracle.generate(fo, want["nbr_pos"], k, want["n0"], np_(xi).astype(np.float64))
+    assert rel_norm(np_(vf), v_or) < 1e-4
+    n_f = np_(gpu_lib.nll_fused(g, K, vf))[0]
+    n_s = np_(gpu_lib.nll(g, f, vf))[0]
+    assert abs(n_f - n_s) <= 1e-12 * abs(n_s)

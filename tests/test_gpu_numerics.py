@@ -144,7 +144,7 @@ def test_fp64_rescue_of_ill_conditioned_rows(gpu_lib, k):
     v = np_(gpu_lib.generate(g, f, to_gpu(xi)))
     assert np.isfinite(v).all()
     assert rel_norm(v, oracle.generate(fo, want["nbr_pos"], k, 256, xi.astype(np.float64))) < tol
-    if k <= 16:
+    if k <= 32:
         vf = np_(gpu_lib.generate_fused(g, gpu_lib.Kernel(*kern, rescue_tol=LDR_RESCUE), to_gpu(xi)))
         assert np.array_equal(vf.view(np.uint32), v.view(np.uint32))
     vbar, tb = gpu_lib.nll_backward(g, f, to_gpu(v))
