@@ -120,14 +120,22 @@ def _percentiles(lat):
                 max_ms=float(a.max() * 1e3))
 
 
+OP_NAMES = {GENERATE: "generate", WHITEN: "whiten", LOGDET: "logdet", NLL_GRAD: "nll_grad"}
+
+
 def run_stream(reqs, inputs, server: Server | None = None, instances=None, stream=None):
     """Drives `reqs` in real time.  inputs[i] is a pinned host float32 tensor
     (the request input of instance i).  With `server`, requests go to the
     engine; otherwise `instances[i] = (graph, factor)` are served one at a time
-    on one stream with the plain API.  Returns latencies and throughput."""
+    on one stream with the plain API.  Returns latency percentiles (overall
+    and per operation), the split of each latency into queue wait (arrival
+    to admission on a slot, or to the start of service one at a time) and
+    service (admission to completion: copies in, device work, copies out),
+    the number of failed requests, and the throughput."""
     from . import generate as gen, logdet as ld, nll, nll_backward, whiten as wh
     t0 = time.monotonic() + 0.05
-    lat, done_at = [], []
+    lat, done_at, queue, service, ops = [], [], [], [], []
+    errors = 0
     if server is not None:
         tickets = []
         for r in reqs:
@@ -135,11 +143,15 @@ def run_stream(reqs, inputs, server: Server | None = None, instances=None, strea
             if wait > 0:
                 time.sleep(wait)
             tickets.append(server.submit(r.inst, r.op, inputs[r.inst], arrival=t0 + r.arrival))
-        for tk in tickets:
+        for r, tk in zip(reqs, tickets):
             st, arr, adm, done = server.wait(tk)
             if st != 0:
-                raise RuntimeError(f"request failed: {st}")
+                errors += 1
+                continue
             lat.append(done - arr)
+            queue.append(adm - arr)
+            service.append(done - adm)
+            ops.append(r.op)
             done_at.append(done)
     else:
         s = torch.cuda.current_stream() if stream is None else stream
@@ -154,6 +166,7 @@ def run_stream(reqs, inputs, server: Server | None = None, instances=None, strea
             wait = t0 + r.arrival - time.monotonic()
             if wait > 0:
                 time.sleep(wait)
+            start = time.monotonic()
             g, f = instances[r.inst]
             din, dout, hout = dev[r.inst]
             if r.op != LOGDET:
@@ -175,9 +188,29 @@ def run_stream(reqs, inputs, server: Server | None = None, instances=None, strea
             s.synchronize()
             now = time.monotonic()
             lat.append(now - (t0 + r.arrival))
+            queue.append(start - (t0 + r.arrival))
+            service.append(now - start)
+            ops.append(r.op)
             done_at.append(now)
     span = max(done_at) - t0 if done_at else 0.0
-    res = _percentiles(lat)
-    res.update(requests=len(lat), throughput_rps=len(lat) / span if span > 0 else 0.0,
-               span_s=span)
+    res = _percentiles(lat) if lat else {}
+    res.update(requests=len(lat), errors=errors,
+               throughput_rps=len(lat) / span if span > 0 else 0.0, span_s=span)
+    if lat:
+        q, sv = np.asarray(queue), np.asarray(service)
+        res["queue_p50_ms"] = float(np.percentile(q, 50) * 1e3)
+        res["queue_p99_ms"] = float(np.percentile(q, 99) * 1e3)
+        res["service_p50_ms"] = float(np.percentile(sv, 50) * 1e3)
+        res["service_p99_ms"] = float(np.percentile(sv, 99) * 1e3)
+        opa = np.asarray(ops)
+        res["per_op"] = {}
+        for op, name in OP_NAMES.items():
+            m = opa == op
+            if m.any():
+                la = np.asarray(lat)[m]
+                res["per_op"][name] = {
+                    "requests": int(m.sum()), "p50_ms": float(np.percentile(la, 50) * 1e3),
+                    "p99_ms": float(np.percentile(la, 99) * 1e3),
+                    "service_p50_ms": float(np.percentile(sv[m], 50) * 1e3),
+                    "service_p99_ms": float(np.percentile(sv[m], 99) * 1e3)}
     return res
