@@ -266,6 +266,34 @@ int graphgp_nll_backward(graphgp_graph_t g, graphgp_factor_t f,
                          const float* v_d, double nllbar, float* vbar_d,
                          double* thetabar_d, void* stream);
 
+/* ---- position ranges (sharding factor, NLL and NLL gradient) ------------
+ * Not a paper operation: the pieces with which several GPUs (one process
+ * each) split the factor, the NLL and its gradient by contiguous ranges of
+ * graph positions (the conditionals of Eq. 2 are independent per point once
+ * the neighbours' coordinates and field values are known).  Each process
+ * holds the whole graph; the sums over disjoint ranges that cover 0..N add
+ * up to graphgp_factor's log-determinant, graphgp_nll and
+ * graphgp_nll_backward.
+ * graphgp_factor_rows: a factor handle holding the conditionals of positions
+ *   [pos_begin, pos_end) only; pos_begin is 0 (the dense block is then
+ *   factored too, and pos_end >= n0 is required) or >= n0.  b and sigma of
+ *   other positions are zero.  Its logdet covers its own positions.  Such a
+ *   handle is accepted only by graphgp_factor_export, graphgp_logdet,
+ *   graphgp_sync_status and the two calls below; the whole-graph sweeps and
+ *   adjoints return GRAPHGP_ERR_INVALID for it.
+ * graphgp_nll_rows: out_d[0] = 0.5 sum_{own i} xi_i^2 + 0.5 logdet(f), with
+ *   v_d float[N] valid at the own positions and at every neighbour of them.
+ * graphgp_nll_backward_rows: the own positions' part of the NLL gradient
+ *   times nllbar: ACCUMULATED into vbar_d float[N] (own positions and their
+ *   neighbours; sum vbar_d over the ranges) and into thetabar_d double[3].
+ *   Uses the graph's work vectors (do not overlap with other calls on it). */
+int graphgp_factor_rows(graphgp_graph_t g, const graphgp_kernel* kern, int64_t pos_begin,
+                        int64_t pos_end, void* stream, graphgp_factor_t* out);
+int graphgp_nll_rows(graphgp_graph_t g, graphgp_factor_t f, const float* v_d, double* out_d,
+                     void* stream);
+int graphgp_nll_backward_rows(graphgp_graph_t g, graphgp_factor_t f, const float* v_d,
+                              double nllbar, float* vbar_d, double* thetabar_d, void* stream);
+
 /* Gradient of nll(v) times nllbar with respect to the point coordinates
  * (Sec. 2.3's derivatives carried through the stationary kernel kappa(r) to
  * the points), with the graph -- order, neighbour lists, depth levels --

@@ -98,6 +98,9 @@ def load() -> ctypes.CDLL:
             "graphgp_nll_backward_points": [_P, _P, _P, ctypes.c_double, _P, _P],
             "graphgp_selftest_wait_timeout": [_I64, _P],
             "graphgp_binary_version": [_P],
+            "graphgp_factor_rows": [_P, _P, _I64, _I64, _P, _P],
+            "graphgp_nll_rows": [_P, _P, _P, _P, _P],
+            "graphgp_nll_backward_rows": [_P, _P, _P, ctypes.c_double, _P, _P, _P],
             "graphgp_generate_fused": [_P, _P, _P, _P, _P, _P],
             "graphgp_whiten_fused": [_P, _P, _P, _P, _P, _P, _P],
             "graphgp_nll_fused": [_P, _P, _P, _P, _P, _P],
@@ -267,6 +270,37 @@ def factor(graph: Graph, kernel: Kernel, stream=None) -> Factor:
     _check(load().graphgp_factor(graph.handle, ctypes.byref(kc), _stream(stream), ctypes.byref(h)),
            "factor")
     return Factor(h, graph, kernel)
+
+
+def factor_rows(graph: Graph, kernel: Kernel, pos_begin: int, pos_end: int, stream=None) -> Factor:
+    """graphgp_factor_rows: the conditionals of positions [pos_begin, pos_end)."""
+    h = ctypes.c_void_p()
+    kc = kernel._c()
+    _check(load().graphgp_factor_rows(graph.handle, ctypes.byref(kc), int(pos_begin),
+                                      int(pos_end), _stream(stream), ctypes.byref(h)),
+           "factor_rows")
+    return Factor(h, graph, kernel)
+
+
+def nll_rows(graph: Graph, fac: Factor, v: torch.Tensor, out: torch.Tensor | None = None,
+             stream=None) -> torch.Tensor:
+    """graphgp_nll_rows: the own positions' part of the NLL (float64[1])."""
+    o = torch.empty(1, dtype=torch.float64, device="cuda") if out is None else out
+    _check(load().graphgp_nll_rows(graph.handle, fac.handle, _dev(v, torch.float32, graph.N, "v"),
+                                   _dev(o, torch.float64, 1, "out"), _stream(stream)), "nll_rows")
+    return o
+
+
+def nll_backward_rows(graph: Graph, fac: Factor, v: torch.Tensor, vbar: torch.Tensor,
+                      thetabar: torch.Tensor, nllbar: float = 1.0, stream=None):
+    """graphgp_nll_backward_rows: adds the own positions' gradient part to
+    vbar (float32[N]) and thetabar (float64[3])."""
+    _check(load().graphgp_nll_backward_rows(graph.handle, fac.handle,
+                                            _dev(v, torch.float32, graph.N, "v"), float(nllbar),
+                                            _dev(vbar, torch.float32, graph.N, "vbar"),
+                                            _dev(thetabar, torch.float64, 3, "thetabar"),
+                                            _stream(stream)), "nll_backward_rows")
+    return vbar, thetabar
 
 
 def sync_status(graph=None, fac=None, stream=None):

@@ -615,8 +615,9 @@ __global__ void scale_kernel(const float* __restrict__ x, float s, float* __rest
 template <int G>
 int launch_factor_backward(graphgp_graph_t g, graphgp_factor_t f, int mode, const float* coef,
                            float beta, const float* v, const float* xi, float* xibar,
-                           double* thetabar, cudaStream_t s) {
-  int64_t npts = g->N - g->n0;
+                           double* thetabar, const int32_t* nbr, int64_t N, int64_t n0v,
+                           cudaStream_t s) {
+  int64_t npts = N - n0v;
   if (npts <= 0) return GRAPHGP_OK;
   constexpr int PPW = 32 / G;
   unsigned grid = grid_for((npts + 4 * PPW - 1) / (4 * PPW) * 128, 128, 16);
@@ -629,11 +630,11 @@ int launch_factor_backward(graphgp_graph_t g, graphgp_factor_t f, int mode, cons
   GGP_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), s));
   const unsigned rgrid = (unsigned)num_sms() * 2;
 #define GGP_FB(KT)                                                                          \
-  factor_backward_kernel<G, KT><<<grid, 128, 0, s>>>(g->xs, g->nbr, g->N, g->k, g->kp, g->n0, \
+  factor_backward_kernel<G, KT><<<grid, 128, 0, s>>>(g->xs, nbr, N, g->k, g->kp, n0v, \
                                                      kf, mode, coef, beta, v, xi, xibar,     \
                                                      thetabar, rows, cnt);                   \
   factor_backward_rescue_kernel<G, KT><<<rgrid, 128, 0, s>>>(                               \
-      g->xs, g->nbr, g->k, g->kp, g->n0, kf, mode, coef, beta, v, xi, xibar, thetabar, rows, cnt, \
+      g->xs, nbr, g->k, g->kp, n0v, kf, mode, coef, beta, v, xi, xibar, thetabar, rows, cnt, \
       (unsigned long long)npts)
   switch (f->kern.type) {
     case GRAPHGP_MATERN12: GGP_FB(GRAPHGP_MATERN12); break;
@@ -651,8 +652,9 @@ constexpr int64_t kBackwardRescueMax = 1 << 20;  // rows listed for the FP64 bac
 template <int K>
 int launch_factor_backward_thread(graphgp_graph_t g, graphgp_factor_t f, int mode,
                                   const float* coef, float beta, const float* v, const float* xi,
-                                  float* xibar, double* thetabar, cudaStream_t s) {
-  const int64_t npts = g->N - g->n0;
+                                  float* xibar, double* thetabar, const int32_t* nbr,
+                                  int64_t N, int64_t n0v, cudaStream_t s) {
+  const int64_t npts = N - n0v;
   if (npts <= 0) return GRAPHGP_OK;
   const unsigned grid = grid_for(npts, 128, 8);
   KernF kf = make_kernf(f->kern);
@@ -668,10 +670,10 @@ int launch_factor_backward_thread(graphgp_graph_t g, graphgp_factor_t f, int mod
 #define GGP_FBT(KT)                                                                             \
   GGP_CUDA(allow_dyn_smem(factor_backward_thread_kernel<K, KT>, smem));                         \
   factor_backward_thread_kernel<K, KT><<<grid, kThreadBlock, smem, s>>>(                        \
-      g->xs, g->nbr, g->N, g->k, g->n0, kf, mode, coef, beta, v, xi, xibar, thetabar, rows, cnt, \
+      g->xs, nbr, N, g->k, n0v, kf, mode, coef, beta, v, xi, xibar, thetabar, rows, cnt, \
       cap);                                                                                     \
   factor_backward_rescue_kernel<K, KT><<<rgrid, 128, 0, s>>>(                                   \
-      g->xs, g->nbr, g->k, g->kp, g->n0, kf, mode, coef, beta, v, xi, xibar, thetabar, rows, cnt, cap)
+      g->xs, nbr, g->k, g->kp, n0v, kf, mode, coef, beta, v, xi, xibar, thetabar, rows, cnt, cap)
   switch (f->kern.type) {
     case GRAPHGP_MATERN12: GGP_FBT(GRAPHGP_MATERN12); break;
     case GRAPHGP_MATERN32: GGP_FBT(GRAPHGP_MATERN32); break;
@@ -685,8 +687,9 @@ int launch_factor_backward_thread(graphgp_graph_t g, graphgp_factor_t f, int mod
 
 int launch_factor_backward_wide(graphgp_graph_t g, graphgp_factor_t f, int mode,
                                 const float* coef, float beta, const float* v, const float* xi,
-                                float* xibar, double* thetabar, cudaStream_t s) {
-  const int64_t npts = g->N - g->n0;
+                                float* xibar, double* thetabar, const int32_t* nbr,
+                                  int64_t N, int64_t n0v, cudaStream_t s) {
+  const int64_t npts = N - n0v;
   if (npts <= 0) return GRAPHGP_OK;
   constexpr int kWarps = 4;
   const size_t smem = kWarps * sizeof(WideWarp);
@@ -703,10 +706,10 @@ int launch_factor_backward_wide(graphgp_graph_t g, graphgp_factor_t f, int mode,
   GGP_CUDA(cudaFuncSetAttribute(factor_backward_wide_kernel<KT>,                               \
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));      \
   factor_backward_wide_kernel<KT><<<grid, 32 * kWarps, smem, s>>>(                             \
-      g->xs, g->nbr, g->N, g->k, g->kp, g->n0, kf, mode, coef, beta, v, xi, xibar, thetabar,   \
+      g->xs, nbr, N, g->k, g->kp, n0v, kf, mode, coef, beta, v, xi, xibar, thetabar,   \
       rows, cnt);                                                                              \
   factor_backward_rescue_kernel<kWideK, KT><<<rgrid, 128, 0, s>>>(                             \
-      g->xs, g->nbr, g->k, g->kp, g->n0, kf, mode, coef, beta, v, xi, xibar, thetabar, rows, cnt,  \
+      g->xs, nbr, g->k, g->kp, n0v, kf, mode, coef, beta, v, xi, xibar, thetabar, rows, cnt,  \
       (unsigned long long)npts)
   switch (f->kern.type) {
     case GRAPHGP_MATERN12: GGP_FBW(GRAPHGP_MATERN12); break;
@@ -719,23 +722,31 @@ int launch_factor_backward_wide(graphgp_graph_t g, graphgp_factor_t f, int mode,
   return GRAPHGP_OK;
 }
 
-int factor_backward(graphgp_graph_t g, graphgp_factor_t f, int mode, const float* coef,
-                    float beta, const float* v, const float* xi, float* xibar, double* thetabar,
-                    cudaStream_t s) {
+int factor_backward_rows(graphgp_graph_t g, graphgp_factor_t f, int mode, const float* coef,
+                         float beta, const float* v, const float* xi, float* xibar,
+                         double* thetabar, int64_t t0, int64_t t1, cudaStream_t s) {
+  if (t1 <= t0) return GRAPHGP_OK;
+  const int32_t* nb = g->nbr + t0 * g->kp;
+  const int64_t N = g->n0 + t1, n0v = g->n0 + t0;
   switch (g->kp) {
-    case 4: return launch_factor_backward_thread<4>(g, f, mode, coef, beta, v, xi, xibar, thetabar, s);
-    case 8: return launch_factor_backward_thread<8>(g, f, mode, coef, beta, v, xi, xibar, thetabar, s);
-    case 12: return launch_factor_backward_thread<12>(g, f, mode, coef, beta, v, xi, xibar, thetabar, s);
-    case 16: return launch_factor_backward_thread<16>(g, f, mode, coef, beta, v, xi, xibar, thetabar, s);
+    case 4: return launch_factor_backward_thread<4>(g, f, mode, coef, beta, v, xi, xibar, thetabar, nb, N, n0v, s);
+    case 8: return launch_factor_backward_thread<8>(g, f, mode, coef, beta, v, xi, xibar, thetabar, nb, N, n0v, s);
+    case 12: return launch_factor_backward_thread<12>(g, f, mode, coef, beta, v, xi, xibar, thetabar, nb, N, n0v, s);
+    case 16: return launch_factor_backward_thread<16>(g, f, mode, coef, beta, v, xi, xibar, thetabar, nb, N, n0v, s);
     case 20:
     case 24:
     case 28:
-    case 32: return launch_factor_backward<32>(g, f, mode, coef, beta, v, xi, xibar, thetabar, s);
-    default: return launch_factor_backward_wide(g, f, mode, coef, beta, v, xi, xibar, thetabar, s);
+    case 32: return launch_factor_backward<32>(g, f, mode, coef, beta, v, xi, xibar, thetabar, nb, N, n0v, s);
+    default: return launch_factor_backward_wide(g, f, mode, coef, beta, v, xi, xibar, thetabar, nb, N, n0v, s);
   }
 }
 
-// Dense block backward from Lbar0 (built from u, xi_0 by dense_lbar_kernel).
+int factor_backward(graphgp_graph_t g, graphgp_factor_t f, int mode, const float* coef,
+                    float beta, const float* v, const float* xi, float* xibar, double* thetabar,
+                    cudaStream_t s) {
+  return factor_backward_rows(g, f, mode, coef, beta, v, xi, xibar, thetabar, 0, g->N - g->n0, s);
+}
+
 }  // namespace
 
 // Kbar_00 (n0 x n0, row-major, every entry a cotangent) of the dense block
@@ -878,11 +889,156 @@ int run_generate_backward(graphgp_graph_t g, graphgp_factor_t f, const float* xi
 int run_whiten(graphgp_graph_t g, graphgp_factor_t f, const float* v, float* xi, double* sq,
                cudaStream_t s);
 
+// ---- row ranges (sharding by position range) ---------------------------------
+// The NLL and its gradient restricted to the positions [p0, p1) whose factor a
+// row-range handle holds: the sums over disjoint ranges add up to the whole.
+
+// sum_e b_e v[c_e] of one row in the stored sweeps' order (gen_lanes slices,
+// two alternating accumulators per slice, slices combined as their xor
+// shuffles do), so xi is bit-identical to the whiten sweep's.
+__device__ __forceinline__ float row_dot_stored_order(const float* __restrict__ b,
+                                                      const int32_t* __restrict__ c, int kp,
+                                                      const float* __restrict__ v) {
+  const int lanes = gen_lanes(kp), hp = kp / lanes;
+  float part[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  for (int h = 0; h < lanes; h++) {
+    float acc0 = 0.0f, acc1 = 0.0f;
+    for (int e = h * hp; e < (h + 1) * hp; e += 4) {
+      acc0 = fmaf(b[e], v[c[e]], acc0);
+      acc1 = fmaf(b[e + 1], v[c[e + 1]], acc1);
+      acc0 = fmaf(b[e + 2], v[c[e + 2]], acc0);
+      acc1 = fmaf(b[e + 3], v[c[e + 3]], acc1);
+    }
+    part[h] = acc0 + acc1;
+  }
+  if (lanes == 4) return (part[0] + part[2]) + (part[1] + part[3]);
+  if (lanes == 2) return part[0] + part[1];
+  return part[0];
+}
+
+// xi_i = (v_i - b_i . v_c(i)) / sigma_i for rows t in [t0, t1); optional FP64
+// sum of xi_i^2 (added to *sq).
+__global__ void whiten_rows_kernel(const int32_t* __restrict__ nbr, const float* __restrict__ b,
+                                   const float* __restrict__ sigma, const float* __restrict__ v,
+                                   float* __restrict__ xi, int kp, int64_t n0, int64_t t0,
+                                   int64_t t1, double* __restrict__ sq) {
+  double local = 0.0;
+  for (int64_t t = t0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < t1;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = n0 + t;
+    const float acc = row_dot_stored_order(b + t * kp, nbr + t * kp, kp, v);
+    const float out = (v[i] - acc) / sigma[i];
+    xi[i] = out;
+    local += (double)out * (double)out;
+  }
+  if (sq) block_add_double(local, sq);
+}
+
+// Transposed gather of whiten's rows [t0, t1), scattered: vbar_i +=
+// xibar_i / sigma_i, vbar_c -= xibar_i b_ic / sigma_i (atomic adds: the
+// neighbours of a range belong to other rows and ranges).
+__global__ void whiten_rows_vjp_kernel(const int32_t* __restrict__ nbr, const float* __restrict__ b,
+                                       const float* __restrict__ sigma,
+                                       const float* __restrict__ xibar, float* vbar, int k, int kp,
+                                       int64_t n0, int64_t t0, int64_t t1) {
+  for (int64_t t = t0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < t1;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = n0 + t;
+    const float a = xibar[i] / sigma[i];
+    atomicAdd(vbar + i, a);
+    for (int e = 0; e < k; e++) atomicAdd(vbar + nbr[t * kp + e], -a * b[t * kp + e]);
+  }
+}
+
+// y[m] += sum_{i >= m} M[i][m] x[i] for the n0 x n0 lower-triangular M.
+__global__ void dense_tmatvec_acc_kernel(const float* __restrict__ M, const float* __restrict__ x,
+                                         float* __restrict__ y, int n0) {
+  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < n0; m += gridDim.x * blockDim.x) {
+    float s = 0.0f;
+    for (int i = m; i < n0; i++) s = fmaf(M[(int64_t)i * n0 + m], x[i], s);
+    y[m] += s;
+  }
+}
+
+__global__ void nll_rows_finish_kernel(const double* __restrict__ sq,
+                                       const double* __restrict__ logdet,
+                                       double* __restrict__ out) {
+  out[0] = 0.5 * sq[0] + 0.5 * logdet[0];
+}
+
+// xi over the factor's positions into xi (full length; other entries untouched).
+int whiten_rows(graphgp_graph_t g, graphgp_factor_t f, const float* v, float* xi, double* sq,
+                cudaStream_t s) {
+  const int64_t p0 = f->row_begin, p1 = f->row_end;
+  if (p0 == 0) GGP_TRY(dense_matvec(f->L0inv, v, xi, g->n0, sq, s));
+  const int64_t t0 = std::max<int64_t>(p0, g->n0) - g->n0, t1 = p1 - g->n0;
+  if (t1 > t0) {
+    whiten_rows_kernel<<<grid_for(t1 - t0, 256), 256, 0, s>>>(g->nbr, f->b, f->sigma, v, xi, g->kp,
+                                                              g->n0, t0, t1, sq);
+    GGP_CUDA(cudaGetLastError());
+  }
+  return GRAPHGP_OK;
+}
+
 }  // namespace ggp
 
 using namespace ggp;
 
-static bool pair_ok(graphgp_graph_t g, graphgp_factor_t f) { return g && f && f->g == g; }
+static bool rows_ok(graphgp_graph_t g, graphgp_factor_t f) {
+  return g && f && f->g == g && f->row_end >= 0;
+}
+
+extern "C" int graphgp_nll_rows(graphgp_graph_t g, graphgp_factor_t f, const float* v_d,
+                                double* out_d, void* stream) {
+  if (!rows_ok(g, f) || !v_d || !out_d) return GRAPHGP_ERR_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  Scratch sc(s);
+  double* sq = nullptr;
+  GGP_TRY(sc.alloc(&sq, 1));
+  GGP_CUDA(cudaMemsetAsync(sq, 0, sizeof(double), s));
+  GGP_TRY(whiten_rows(g, f, v_d, g->tmp_vec2, sq, s));
+  nll_rows_finish_kernel<<<1, 1, 0, s>>>(sq, f->logdet, out_d);
+  GGP_CUDA(cudaGetLastError());
+  return GRAPHGP_OK;
+}
+
+extern "C" int graphgp_nll_backward_rows(graphgp_graph_t g, graphgp_factor_t f, const float* v_d,
+                                         double nllbar, float* vbar_d, double* thetabar_d,
+                                         void* stream) {
+  if (!rows_ok(g, f) || !v_d || !vbar_d || !thetabar_d) return GRAPHGP_ERR_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  float* xi = g->tmp_vec2;
+  float* xibar = g->tmp_vec;
+  GGP_TRY(whiten_rows(g, f, v_d, xi, nullptr, s));
+  scale_kernel<<<grid_for(g->N, 256), 256, 0, s>>>(xi, (float)nllbar, xibar, g->N);
+  GGP_CUDA(cudaGetLastError());
+  const int n0 = g->n0;
+  const int64_t p0 = f->row_begin, p1 = f->row_end;
+  if (p0 == 0) {
+    // dense rows: u_0 = L0^-T xibar_0 into vbar_0, and the dense block's theta part
+    Scratch sc(s);
+    float* u0 = nullptr;
+    GGP_TRY(sc.alloc(&u0, n0));
+    dense_lower_tmatvec_kernel<<<(n0 + 255) / 256, 256, 0, s>>>(f->L0inv, xibar, u0, n0);
+    dense_tmatvec_acc_kernel<<<(n0 + 255) / 256, 256, 0, s>>>(f->L0inv, xibar, vbar_d, n0);
+    GGP_CUDA(cudaGetLastError());
+    GGP_TRY(dense_backward(g, f, u0, xi, -1.0f, (float)(0.5 * nllbar), thetabar_d, s));
+  }
+  const int64_t t0 = std::max<int64_t>(p0, n0) - n0, t1 = p1 - n0;
+  if (t1 > t0) {
+    whiten_rows_vjp_kernel<<<grid_for(t1 - t0, 256), 256, 0, s>>>(g->nbr, f->b, f->sigma, xibar,
+                                                                  vbar_d, g->k, g->kp, n0, t0, t1);
+    GGP_CUDA(cudaGetLastError());
+    GGP_TRY(factor_backward_rows(g, f, 0, xibar, (float)nllbar, v_d, xi, nullptr, thetabar_d, t0,
+                                 t1, s));
+  }
+  return GRAPHGP_OK;
+}
+
+
+static bool pair_ok(graphgp_graph_t g, graphgp_factor_t f) {
+  return g && f && f->g == g && f->row_end < 0;
+}
 
 extern "C" int graphgp_generate_backward(graphgp_graph_t g, graphgp_factor_t f, const float* xi_d,
                                          const float* v_d, const float* vbar_d, float* xibar_d,

@@ -164,6 +164,9 @@ struct graphgp_factor_s {
   float* L0inv = nullptr;    // [n0*n0] row-major lower
   double* logdet = nullptr;  // [1]
   unsigned long long* not_pd = nullptr;  // [1]
+  // positions whose conditionals this handle holds: [row_begin, row_end);
+  // row_end < 0 for a whole-graph factor (graphgp_factor)
+  int64_t row_begin = 0, row_end = -1;
 };
 
 namespace ggp {

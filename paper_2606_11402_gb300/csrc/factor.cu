@@ -37,6 +37,15 @@ struct RescueList {
   }
 };
 
+// The rows [t0, t1) of the sparse positions, seen by the factor kernels as a
+// graph of their own: positions n0 + t0 .. n0 + t1 - 1, neighbour and weight
+// rows shifted by t0 (position indices stay global).
+struct RowView {
+  const int32_t* nbr;
+  float* b;
+  int64_t N, n0;
+};
+
 template <int G, int KT>
 __global__ void __launch_bounds__(128) point_factor_kernel(
     const float4* __restrict__ xs, const int32_t* __restrict__ nbr, int64_t N, int k, int kp,
@@ -265,15 +274,15 @@ __global__ void __launch_bounds__(128) factor_rescue_kernel(
 
 template <int KMAX>
 int launch_rescue(int type, graphgp_graph_t g, graphgp_factor_t f, const KernF& kf,
-                  const RescueList& rl, cudaStream_t s) {
+                  const RescueList& rl, const RowView& rv, cudaStream_t s) {
   const unsigned grid = 4 * (unsigned)num_sms();
 #define GGP_RS(KT)                                                                          \
   if constexpr (KMAX <= 32) {                                                               \
     factor_rescue_warp_kernel<KMAX, KT><<<grid, 128, 0, s>>>(                               \
-        g->xs, g->nbr, g->k, g->kp, g->n0, kf, rl, f->b, f->sigma, f->logdet, f->not_pd);   \
+        g->xs, rv.nbr, g->k, g->kp, rv.n0, kf, rl, rv.b, f->sigma, f->logdet, f->not_pd);   \
   } else {                                                                                  \
     factor_rescue_kernel<KMAX, KT><<<grid, 128, 0, s>>>(                                    \
-        g->xs, g->nbr, g->k, g->kp, g->n0, kf, rl, f->b, f->sigma, f->logdet, f->not_pd);   \
+        g->xs, rv.nbr, g->k, g->kp, rv.n0, kf, rl, rv.b, f->sigma, f->logdet, f->not_pd);   \
   }
   switch (type) {
     case GRAPHGP_MATERN12: GGP_RS(GRAPHGP_MATERN12); break;
@@ -561,8 +570,8 @@ __global__ void __launch_bounds__(1024) dense_finish_kernel(
 
 template <int G>
 int launch_point(int type, graphgp_graph_t g, graphgp_factor_t f, const KernF& kf,
-                 const RescueList& rl, cudaStream_t s) {
-  int64_t npts = g->N - g->n0;
+                 const RescueList& rl, const RowView& rv, cudaStream_t s) {
+  int64_t npts = rv.N - rv.n0;
   constexpr int PPW = 32 / G;
   int64_t groups_per_block = 4 * PPW;
   unsigned grid = grid_for((npts + groups_per_block - 1) / groups_per_block * 128, 128, 16);
@@ -570,8 +579,8 @@ int launch_point(int type, graphgp_graph_t g, graphgp_factor_t f, const KernF& k
 #define GGP_PF(KT)                                                                       \
   GGP_CUDA(cudaFuncSetAttribute(point_factor_kernel<G, KT>,                              \
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
-  point_factor_kernel<G, KT><<<grid, 128, smem, s>>>(g->xs, g->nbr, g->N, g->k, g->kp,   \
-                                                     g->n0, kf, f->b, f->sigma, f->logdet, \
+  point_factor_kernel<G, KT><<<grid, 128, smem, s>>>(g->xs, rv.nbr, rv.N, g->k, g->kp,     \
+                                                     rv.n0, kf, rv.b, f->sigma, f->logdet, \
                                                      f->not_pd, rl)
   switch (type) {
     case GRAPHGP_MATERN12: GGP_PF(GRAPHGP_MATERN12); break;
@@ -586,14 +595,14 @@ int launch_point(int type, graphgp_graph_t g, graphgp_factor_t f, const KernF& k
 
 template <int K>
 int launch_point_thread(int type, graphgp_graph_t g, graphgp_factor_t f, const KernF& kf,
-                        const RescueList& rl, cudaStream_t s) {
-  const int64_t npts = g->N - g->n0;
+                        const RescueList& rl, const RowView& rv, cudaStream_t s) {
+  const int64_t npts = rv.N - rv.n0;
   const unsigned grid = grid_for(npts, kThreadBlock, 8);
   constexpr size_t smem = ThreadStage<K>::kBytes + 4 * warp_rescue_bytes<K>();
 #define GGP_PT(KT)                                                                            \
   GGP_CUDA(allow_dyn_smem(point_factor_thread_kernel<K, KT>, smem));                          \
   point_factor_thread_kernel<K, KT><<<grid, kThreadBlock, smem, s>>>(                         \
-      g->xs, g->nbr, g->N, g->k, g->n0, kf, f->b, f->sigma, f->logdet, f->not_pd, rl)
+      g->xs, rv.nbr, rv.N, g->k, rv.n0, kf, rv.b, f->sigma, f->logdet, f->not_pd, rl)
   switch (type) {
     case GRAPHGP_MATERN12: GGP_PT(GRAPHGP_MATERN12); break;
     case GRAPHGP_MATERN32: GGP_PT(GRAPHGP_MATERN32); break;
@@ -609,15 +618,15 @@ constexpr int kWideWarps = 4;  // warps per block of the wide kernels
 constexpr int64_t kRescueListMax = 1 << 20;  // rows listed for the FP64 rescue kernel
 
 int launch_point_wide(int type, graphgp_graph_t g, graphgp_factor_t f, const KernF& kf,
-                      const RescueList& rl, cudaStream_t s) {
-  const int64_t npts = g->N - g->n0;
+                      const RescueList& rl, const RowView& rv, cudaStream_t s) {
+  const int64_t npts = rv.N - rv.n0;
   const size_t smem = kWideWarps * sizeof(WideWarp);
   const unsigned grid = grid_for((npts + kWideWarps - 1) / kWideWarps * 128, 128, 4);
 #define GGP_PW(KT)                                                                           \
   GGP_CUDA(cudaFuncSetAttribute(point_factor_wide_kernel<KT>,                                \
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));    \
   point_factor_wide_kernel<KT><<<grid, 32 * kWideWarps, smem, s>>>(                          \
-      g->xs, g->nbr, g->N, g->k, g->kp, g->n0, kf, f->b, f->sigma, f->logdet, f->not_pd, rl)
+      g->xs, rv.nbr, rv.N, g->k, g->kp, rv.n0, kf, rv.b, f->sigma, f->logdet, f->not_pd, rl)
   switch (type) {
     case GRAPHGP_MATERN12: GGP_PW(GRAPHGP_MATERN12); break;
     case GRAPHGP_MATERN32: GGP_PW(GRAPHGP_MATERN32); break;
@@ -631,10 +640,11 @@ int launch_point_wide(int type, graphgp_graph_t g, graphgp_factor_t f, const Ker
 
 }  // namespace
 
-int point_factor(graphgp_graph_t g, graphgp_factor_t f, const KernF& kf, int type,
-                 cudaStream_t s) {
-  if (g->N <= g->n0) return GRAPHGP_OK;
-  const int64_t npts = g->N - g->n0;
+int point_factor_rows(graphgp_graph_t g, graphgp_factor_t f, const KernF& kf, int type,
+                      int64_t t0, int64_t t1, cudaStream_t s) {
+  if (t1 <= t0) return GRAPHGP_OK;
+  const int64_t npts = t1 - t0;
+  const RowView rv{g->nbr + t0 * g->kp, f->b + t0 * g->kp, g->n0 + t1, g->n0 + t0};
   Scratch sc(s);
   RescueList rl;
   rl.cap = (unsigned long long)std::min<int64_t>(npts, kRescueListMax);
@@ -642,16 +652,21 @@ int point_factor(graphgp_graph_t g, graphgp_factor_t f, const KernF& kf, int typ
   GGP_TRY(sc.alloc(&rl.count, 1));
   GGP_CUDA(cudaMemsetAsync(rl.count, 0, sizeof(unsigned long long), s));
   switch (g->kp) {
-    case 4: GGP_TRY(launch_point_thread<4>(type, g, f, kf, rl, s)); return launch_rescue<4>(type, g, f, kf, rl, s);
-    case 8: GGP_TRY(launch_point_thread<8>(type, g, f, kf, rl, s)); return launch_rescue<8>(type, g, f, kf, rl, s);
-    case 12: GGP_TRY(launch_point_thread<12>(type, g, f, kf, rl, s)); return launch_rescue<12>(type, g, f, kf, rl, s);
-    case 16: GGP_TRY(launch_point_thread<16>(type, g, f, kf, rl, s)); return launch_rescue<16>(type, g, f, kf, rl, s);
+    case 4: GGP_TRY(launch_point_thread<4>(type, g, f, kf, rl, rv, s)); return launch_rescue<4>(type, g, f, kf, rl, rv, s);
+    case 8: GGP_TRY(launch_point_thread<8>(type, g, f, kf, rl, rv, s)); return launch_rescue<8>(type, g, f, kf, rl, rv, s);
+    case 12: GGP_TRY(launch_point_thread<12>(type, g, f, kf, rl, rv, s)); return launch_rescue<12>(type, g, f, kf, rl, rv, s);
+    case 16: GGP_TRY(launch_point_thread<16>(type, g, f, kf, rl, rv, s)); return launch_rescue<16>(type, g, f, kf, rl, rv, s);
     case 20:
     case 24:
     case 28:
-    case 32: GGP_TRY(launch_point<32>(type, g, f, kf, rl, s)); return launch_rescue<32>(type, g, f, kf, rl, s);
-    default: GGP_TRY(launch_point_wide(type, g, f, kf, rl, s)); return launch_rescue<kWideK>(type, g, f, kf, rl, s);
+    case 32: GGP_TRY(launch_point<32>(type, g, f, kf, rl, rv, s)); return launch_rescue<32>(type, g, f, kf, rl, rv, s);
+    default: GGP_TRY(launch_point_wide(type, g, f, kf, rl, rv, s)); return launch_rescue<kWideK>(type, g, f, kf, rl, rv, s);
   }
+}
+
+int point_factor(graphgp_graph_t g, graphgp_factor_t f, const KernF& kf, int type,
+                 cudaStream_t s) {
+  return point_factor_rows(g, f, kf, type, 0, g->N - g->n0, s);
 }
 
 int dense_factor(graphgp_graph_t g, graphgp_factor_t f, const KernF& kf, int type,
@@ -701,18 +716,24 @@ int dense_factor(graphgp_graph_t g, graphgp_factor_t f, const KernF& kf, int typ
 
 using namespace ggp;
 
-extern "C" int graphgp_factor(graphgp_graph_t g, const graphgp_kernel* kern, void* stream,
-                              graphgp_factor_t* out) {
+static int factor_impl(graphgp_graph_t g, const graphgp_kernel* kern, int64_t p0, int64_t p1,
+                       bool rows, void* stream, graphgp_factor_t* out) {
   if (!out) return GRAPHGP_ERR_INVALID;
   *out = nullptr;
   if (!g || !kern || kern->type < 0 || kern->type > 3 || !(kern->sigma2 > 0) ||
       !(kern->lengthscale > 0) || !(kern->nugget >= 0) || !std::isfinite(kern->rescue_tol))
+    return GRAPHGP_ERR_INVALID;
+  if (p0 < 0 || p1 > g->N || p0 > p1 || (p0 > 0 && p0 < g->n0) || (p0 == 0 && p1 < g->n0))
     return GRAPHGP_ERR_INVALID;
   cudaStream_t s = (cudaStream_t)stream;
   graphgp_factor_t f = new (std::nothrow) graphgp_factor_s();
   if (!f) return GRAPHGP_ERR_OOM;
   f->g = g;
   f->kern = *kern;
+  if (rows) {
+    f->row_begin = p0;
+    f->row_end = p1;
+  }
   auto fail = [&](int rc) {
     f->mem.free_all();
     delete f;
@@ -728,13 +749,39 @@ extern "C" int graphgp_factor(graphgp_graph_t g, const graphgp_kernel* kern, voi
     GGP_CUDA(cudaMemsetAsync(f->logdet, 0, 8, s));
     GGP_CUDA(cudaMemsetAsync(f->not_pd, 0, 8, s));
     KernF kf = make_kernf(*kern);
-    GGP_TRY(dense_factor(g, f, kf, kern->type, s));
-    GGP_TRY(point_factor(g, f, kf, kern->type, s));
+    if (rows) {  // rows outside the range stay zero
+      GGP_CUDA(cudaMemsetAsync(f->b, 0, (g->N - g->n0) * g->kp * sizeof(float), s));
+      GGP_CUDA(cudaMemsetAsync(f->sigma, 0, g->N * sizeof(float), s));
+      GGP_CUDA(cudaMemsetAsync(f->L0, 0, (int64_t)g->n0 * g->n0 * sizeof(float), s));
+      GGP_CUDA(cudaMemsetAsync(f->L0inv, 0, (int64_t)g->n0 * g->n0 * sizeof(float), s));
+    }
+    if (p0 == 0) GGP_TRY(dense_factor(g, f, kf, kern->type, s));
+    const int64_t t0 = std::max<int64_t>(p0, g->n0) - g->n0, t1 = std::max<int64_t>(p1 - g->n0, 0);
+    GGP_TRY(point_factor_rows(g, f, kf, kern->type, t0, t1, s));
     return GRAPHGP_OK;
   }();
   if (rc < 0) return fail(rc);
   *out = f;
   return GRAPHGP_OK;
+}
+
+extern "C" int graphgp_factor(graphgp_graph_t g, const graphgp_kernel* kern, void* stream,
+                              graphgp_factor_t* out) {
+  if (!g) {
+    if (out) *out = nullptr;
+    return GRAPHGP_ERR_INVALID;
+  }
+  return factor_impl(g, kern, 0, g->N, false, stream, out);
+}
+
+extern "C" int graphgp_factor_rows(graphgp_graph_t g, const graphgp_kernel* kern,
+                                   int64_t pos_begin, int64_t pos_end, void* stream,
+                                   graphgp_factor_t* out) {
+  if (!g) {
+    if (out) *out = nullptr;
+    return GRAPHGP_ERR_INVALID;
+  }
+  return factor_impl(g, kern, pos_begin, pos_end, true, stream, out);
 }
 
 extern "C" int graphgp_factor_export(graphgp_factor_t f, float* b_d, float* sigma_d, float* L0_d,

@@ -216,7 +216,7 @@ using namespace ggp;
 
 extern "C" int graphgp_nll_noalloc(graphgp_graph_t g, graphgp_factor_t f, const float* v_d,
                                    double* out_d, void* stream) {
-  if (!g || !f || f->g != g || !v_d || !out_d) return GRAPHGP_ERR_INVALID;
+  if (!g || !f || f->g != g || f->row_end >= 0 || !v_d || !out_d) return GRAPHGP_ERR_INVALID;
   if (!g->tile_start || g->num_levels > 8192) {
     std::fprintf(stderr, "graphgp_nll_noalloc: graph has %d depth levels; at most 8192 are "
                          "supported without allocation\n", g->num_levels);

@@ -270,7 +270,7 @@ using namespace ggp;
 extern "C" int graphgp_nll_backward_points(graphgp_graph_t g, graphgp_factor_t f,
                                            const float* v_d, double nllbar, float* pbar_d,
                                            void* stream) {
-  if (!g || !f || f->g != g || !v_d || !pbar_d) return GRAPHGP_ERR_INVALID;
+  if (!g || !f || f->g != g || f->row_end >= 0 || !v_d || !pbar_d) return GRAPHGP_ERR_INVALID;
   cudaStream_t s = (cudaStream_t)stream;
   Scratch sc(s);
   double* acc = nullptr;

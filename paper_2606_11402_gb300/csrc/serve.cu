@@ -268,7 +268,7 @@ extern "C" int graphgp_server_create(int n_slots, size_t hbm_budget, int use_gra
 
 extern "C" int graphgp_server_register(graphgp_server_t sv, graphgp_graph_t g, graphgp_factor_t f,
                                        int* instance_id) {
-  if (!sv || !g || !f || f->g != g || !instance_id) return GRAPHGP_ERR_INVALID;
+  if (!sv || !g || !f || f->g != g || f->row_end >= 0 || !instance_id) return GRAPHGP_ERR_INVALID;
   std::lock_guard<std::mutex> lk(sv->mu);
   if (sv->started) return GRAPHGP_ERR_INVALID;
   // the children CSR of the gradient requests is built now, not under capture

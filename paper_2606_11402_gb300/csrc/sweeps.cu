@@ -485,7 +485,9 @@ int run_whiten(graphgp_graph_t g, graphgp_factor_t f, const float* v, float* xi,
 
 using namespace ggp;
 
-static bool same_graph(graphgp_graph_t g, graphgp_factor_t f) { return g && f && f->g == g; }
+static bool same_graph(graphgp_graph_t g, graphgp_factor_t f) {
+  return g && f && f->g == g && f->row_end < 0;  // whole-graph factors only
+}
 
 extern "C" int graphgp_generate(graphgp_graph_t g, graphgp_factor_t f, const float* xi_d,
                                 float* v_d, void* stream) {
