@@ -369,15 +369,16 @@ __global__ void __launch_bounds__(128) factor_backward_kernel(
         ps += kb;
         pn += kb;
       } else {
-        float d2 = st.D2[c];
-        ps += kb * kappa_d2<KT>(kf, d2) * inv_s2;
-        pl += kb * dkappa_dell_d2<KT>(kf, d2);
+        const KD kd = kappa_dkappa_d2<KT>(kf, st.D2[c]);
+        ps += kb * kd.k * inv_s2;
+        pl += kb * kd.dl;
       }
     }
     {
       float kci = g - 2.0f * sbar * ba;
-      ps += kci * kappa_d2<KT>(kf, st.d2q) * inv_s2;
-      pl += kci * dkappa_dell_d2<KT>(kf, st.d2q);
+      const KD kd = kappa_dkappa_d2<KT>(kf, st.d2q);
+      ps += kci * kd.k * inv_s2;
+      pl += kci * kd.dl;
     }
     if (!real) pl = ps = pn = 0.0f;
     if (a == 0) {  // Kbar_ii = sbar
@@ -460,15 +461,15 @@ __global__ void __launch_bounds__(128) factor_backward_wide_kernel(
           ps += kb;
           pn += kb;
         } else {
-          const float d2 = sqdist(xa, W.x[c]);
-          ps += kb * kappa_d2<KT>(kf, d2) * inv_s2;
-          pl += kb * dkappa_dell_d2<KT>(kf, d2);
+          const KD kd = kappa_dkappa_d2<KT>(kf, sqdist(xa, W.x[c]));
+          ps += kb * kd.k * inv_s2;
+          pl += kb * kd.dl;
         }
       }
       const float kci = ga - 2.0f * sbar * ba;
-      const float d2q = sqdist(xa, xq);
-      ps += kci * kappa_d2<KT>(kf, d2q) * inv_s2;
-      pl += kci * dkappa_dell_d2<KT>(kf, d2q);
+      const KD kq = kappa_dkappa_d2<KT>(kf, sqdist(xa, xq));
+      ps += kci * kq.k * inv_s2;
+      pl += kci * kq.dl;
       tl += pl;
       ts += ps;
       tn += pn;
@@ -572,29 +573,37 @@ __global__ void __launch_bounds__(128) factor_backward_thread_kernel(
 #pragma unroll
     for (int a = 0; a < K; a++) g[a] = a < k ? alpha * v[ca[a]] : 0.0f;
     thread_chol_solve<K>(p, k, g);
-    const float* bb = p.y;
-    // row sums in FP32 (at most k + 1 terms), added to the FP64 totals
-    ts += sbar;  // Kbar_ii = sbar
-    tn += sbar;
-    float4 x[K];  // the staged coordinates (padding: the point itself)
-#pragma unroll
-    for (int a = 0; a < K; a++) x[a] = a < k ? st.X[a * kThreadBlock] : xq;
+    // b and g into the stage (the kernel values there are consumed), then a
+    // rolled loop over the pairs: row sums in FP32 (at most k + 1 terms),
+    // added to the FP64 totals
+    float* sb = st.E;
+    float* sg = st.E + K * kThreadBlock;
 #pragma unroll
     for (int a = 0; a < K; a++) {
-      if (a < k) {
-        const float kaa = -g[a] * bb[a] + sbar * bb[a] * bb[a];
+      sb[a * kThreadBlock] = p.y[a];
+      sg[a * kThreadBlock] = g[a];
+    }
+    ts += sbar;  // Kbar_ii = sbar
+    tn += sbar;
+#pragma unroll 1
+    for (int a = 0; a < k; a++) {
+      const float ga = sg[a * kThreadBlock], ba = sb[a * kThreadBlock];
+      const float4 xa = st.X[a * kThreadBlock];
+      {
+        const float kaa = -ga * ba + sbar * ba * ba;
         float pl = 0.0f, ps = kaa;
-#pragma unroll
+#pragma unroll 1
         for (int c = 0; c < a; c++) {
-          const float kb = (-g[a] * bb[c] + sbar * bb[a] * bb[c]) + (-g[c] * bb[a] + sbar * bb[c] * bb[a]);
-          const float d2 = sqdist(x[a], x[c]);
-          ps += kb * kappa_d2<KT>(kf, d2) * inv_s2;
-          pl += kb * dkappa_dell_d2<KT>(kf, d2);
+          const float gc = sg[c * kThreadBlock], bc = sb[c * kThreadBlock];
+          const float kb = (-ga * bc + sbar * ba * bc) + (-gc * ba + sbar * bc * ba);
+          const KD kd = kappa_dkappa_d2<KT>(kf, sqdist(xa, st.X[c * kThreadBlock]));
+          ps += kb * kd.k * inv_s2;
+          pl += kb * kd.dl;
         }
-        const float kci = g[a] - 2.0f * sbar * bb[a];
-        const float d2q = sqdist(x[a], xq);
-        ps += kci * kappa_d2<KT>(kf, d2q) * inv_s2;
-        pl += kci * dkappa_dell_d2<KT>(kf, d2q);
+        const float kci = ga - 2.0f * sbar * ba;
+        const KD kq = kappa_dkappa_d2<KT>(kf, sqdist(xa, xq));
+        ps += kci * kq.k * inv_s2;
+        pl += kci * kq.dl;
         tl += pl;
         ts += ps;
         tn += kaa;

@@ -272,6 +272,38 @@ __device__ __forceinline__ float dkappa_dell_d2(const KernF& p, float d2) {
   }
 }
 
+
+// kappa and d kappa / d lengthscale of one distance from one exponential
+// (the kernel-parameter gradient needs both for every covariance entry);
+// the same values as kappa_d2 and dkappa_dell_d2.
+struct KD {
+  float k, dl;
+};
+
+template <int KT>
+__device__ __forceinline__ KD kappa_dkappa_d2(const KernF& p, float d2) {
+  const float il = p.inv_ell;
+  if (KT == GRAPHGP_SQEXP) {
+    const float e = expf(-0.5f * d2 * il * il);
+    return KD{p.s2 * e, p.s2 * e * d2 * il * il * il};
+  } else {
+    const float r = sqrtf(d2);
+    if (KT == GRAPHGP_MATERN12) {
+      const float e = expf(-r * il);
+      return KD{p.s2 * e, p.s2 * e * r * il * il};
+    } else if (KT == GRAPHGP_MATERN32) {
+      const float a = 1.7320508075688772f * r * il;
+      const float e = expf(-a);
+      return KD{p.s2 * (1.0f + a) * e, p.s2 * a * a * e * il};
+    } else {
+      const float a = 2.2360679774997896f * r * il;
+      const float e = expf(-a);
+      return KD{p.s2 * (1.0f + a + a * a * (1.0f / 3.0f)) * e,
+                p.s2 * a * a * (1.0f + a) * e * il * (1.0f / 3.0f)};
+    }
+  }
+}
+
 __device__ __forceinline__ float sqdist(float4 a, float4 b) {
   float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
   return fmaf(dz, dz, fmaf(dy, dy, dx * dx));
