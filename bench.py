@@ -346,7 +346,7 @@ def differentiation_bench(stream, reps=3):
     def step():
         gg.nll(g, f, v, out=out)
         gg.nll_backward(g, f, v, vbar=vbar, thetabar=tbar)
-    step()  # builds the children CSR
+    step()
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record(stream)
@@ -656,7 +656,7 @@ def run_ours(args):
         fused["generate_points_per_s"] = N / (fused["generate_ms"] / 1e3)
         fused["whiten_points_per_s"] = N / (fused["whiten_ms"] / 1e3)
 
-    # adjoints on the same workload (children CSR built by the untimed first call)
+    # adjoints on the same workload
     def timed_ms(fn, reps=3):
         fn()
         torch.cuda.synchronize()

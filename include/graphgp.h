@@ -190,7 +190,9 @@ int graphgp_sync_status(graphgp_graph_t g, graphgp_factor_t f, void* stream,
  *           v_i = b_i . v_c(i) + sigma_i xi_i.
  * whiten:   xi = L^-1 v, i.e. xi_0 = L0^-1 v_0, xi_i = (v_i - b_i.v_c(i))/sigma_i.
  * logdet:   out_d[0] = log det(L L^T) = 2 sum log sigma_i (double, device).
- * nll:      out_d[0] = 0.5 xi.xi + 0.5 logdet with xi = whiten(v) (double). */
+ * nll:      out_d[0] = 0.5 xi.xi + 0.5 logdet with xi = whiten(v) (double).
+ * generate's v_d must not overlap xi_d (GRAPHGP_ERR_INVALID): v_d is written
+ * while xi_d is still being read. */
 int graphgp_generate(graphgp_graph_t g, graphgp_factor_t f, const float* xi_d,
                      float* v_d, void* stream);
 int graphgp_whiten(graphgp_graph_t g, graphgp_factor_t f, const float* v_d,
@@ -253,7 +255,10 @@ int graphgp_nll_fused(graphgp_graph_t g, const graphgp_kernel* kern, const float
  *   xibar_d (overwritten) and adds the kernel-parameter gradient.
  * whiten_backward: given xibar = dL/dxi for xi = whiten(v) and a scalar
  *   logdetbar = dL/dlogdet, writes vbar_d (overwritten) and adds thetabar.
- * nll_backward: gradient of nll(v) times nllbar: vbar_d, thetabar_d. */
+ * nll_backward: gradient of nll(v) times nllbar: vbar_d, thetabar_d.
+ * The transposed sums (a position's cotangent from all rows that condition
+ * on it) are formed with atomic adds, so vbar_d / xibar_d and thetabar_d
+ * agree between calls to rounding, not bit for bit. */
 int graphgp_generate_backward(graphgp_graph_t g, graphgp_factor_t f,
                               const float* xi_d, const float* v_d,
                               const float* vbar_d, float* xibar_d,
@@ -333,8 +338,7 @@ enum { GRAPHGP_OP_GENERATE = 0, GRAPHGP_OP_WHITEN = 1, GRAPHGP_OP_LOGDET = 2,
 
 int graphgp_server_create(int n_slots, size_t hbm_budget, int use_graphs,
                           graphgp_server_t* out);
-/* Before graphgp_server_start only.  Builds the instance's children CSR
- * (synchronises the device). */
+/* Before graphgp_server_start only (synchronises the device). */
 int graphgp_server_register(graphgp_server_t sv, graphgp_graph_t g,
                             graphgp_factor_t f, int* instance_id);
 int graphgp_server_start(graphgp_server_t sv);

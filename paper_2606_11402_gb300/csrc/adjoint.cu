@@ -3,12 +3,13 @@
 //
 // With every sparse row written as v_i = b_i . v_c(i) + sigma_i xi_i:
 //  * whiten VJP (xi = L^-1 v, cotangent xibar, logdetbar), w_i = xibar_i/sigma_i:
-//      vbar_i = w_i - sum over children (j, a) of i of w_j b_ja   (transposed
-//      gather over the children CSR), bbar_i = -w_i v_c, sigbar_i =
+//      vbar_i = w_i - sum over children (j, a) of i of w_j b_ja   (every row
+//      j scatters -w_j b_ja to its neighbours), bbar_i = -w_i v_c, sigbar_i =
 //      -w_i xi_i + 2 logdetbar / sigma_i;
 //  * generate VJP (v = L xi, cotangent vbar): u = (I - B)^-T vbar by a reverse
-//      level sweep, u_j = vbar_j + sum over children (i, a) of j of b_ia u_i;
-//      xibar_i = sigma_i u_i, bbar_i = u_i v_c, sigbar_i = u_i xi_i;
+//      level sweep, u_j = vbar_j + sum over children (i, a) of j of b_ia u_i
+//      (every row i, once u_i is complete, scatters b_ia u_i to its
+//      neighbours); xibar_i = sigma_i u_i, bbar_i = u_i v_c, sigbar_i = u_i xi_i;
 //  * factor backward, per row, from b = K_cc^-1 K_ci and s = sigma^2:
 //      sbar = sigbar/(2 sigma), g = K_cc^-1 bbar, Kbar_cc = -g b^T + sbar b b^T,
 //      Kbar_ci = g - 2 sbar b, Kbar_ii = sbar, theta_bar += sum Kbar dK/dtheta.
@@ -24,29 +25,6 @@
 
 namespace ggp {
 namespace {
-
-// ---- children CSR -----------------------------------------------------------
-__global__ void edge_keys_kernel(const int32_t* __restrict__ nbr, int64_t rows, int k, int kp,
-                                 uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
-  int64_t E = rows * k;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    int64_t r = e / k;
-    int a = (int)(e - r * k);
-    keys[e] = (uint32_t)nbr[r * kp + a];
-    vals[e] = (uint32_t)(r * kp + a);
-  }
-}
-
-__global__ void rowptr_kernel(const uint32_t* __restrict__ keys, int64_t E, int64_t N,
-                              int64_t* __restrict__ rowptr) {
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e <= E;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    int64_t prev = e == 0 ? -1 : (int64_t)keys[e - 1];
-    int64_t cur = e == E ? N : (int64_t)keys[e];
-    for (int64_t q = prev + 1; q <= cur; q++) rowptr[q] = e;
-  }
-}
 
 // ---- dense helpers ------------------------------------------------------------
 // y_m = sum_{i >= m} M[i][m] x_i (transpose of a lower-triangular n0 x n0 M)
@@ -142,175 +120,129 @@ __global__ void dense_theta_kernel(const float* __restrict__ Kbar, const float4*
   block_add3(tl, ts, tn, thetabar);
 }
 
-// ---- whiten VJP: transposed gather ------------------------------------------------
-// vbar_p = base_p - sum over children (j, slot) of w_j b_j,slot, with
-// w_j = xibar_j / sigma_j; base_p = w_p for sparse p and (L0^-T xibar_0)_p
-// (already in vbar) for dense p.
-__global__ void whiten_transpose_kernel(const int64_t* __restrict__ rowptr,
-                                        const int32_t* __restrict__ cedge, int kp, int64_t n0,
-                                        const float* __restrict__ b, const float* __restrict__ sigma,
-                                        const float* __restrict__ xibar, float* __restrict__ vbar,
-                                        int64_t N) {
-  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < N;
-       p += (int64_t)gridDim.x * blockDim.x) {
-    float acc = p < n0 ? vbar[p] : xibar[p] / sigma[p];
-    for (int64_t e = rowptr[p]; e < rowptr[p + 1]; e++) {
-      int32_t ce = cedge[e];
-      int64_t j = ce / kp + n0;
-      acc = fmaf(-(xibar[j] / sigma[j]), b[ce], acc);
-    }
-    vbar[p] = acc;
+// ---- adjoint sweeps by scatter ------------------------------------------------
+// Both VJPs apply a transpose of the row operator: entry b_ia of row i moves
+// a cotangent from position i to its neighbour c_a.  Rows are streamed in
+// position order, LANES threads per row as in the forward sweeps (16-byte
+// row loads), and each entry's contribution is added at its neighbour with a
+// fire-and-forget atomic add in L2 (red.global.add.f32).  The additions into
+// one position arrive in no fixed order, so results agree with the ordered
+// sums to rounding, not bit for bit.
+#define GGP_ADJ_KP_DISPATCH(kp, call) \
+  switch (kp) {                       \
+    case 4: call(4); break;           \
+    case 8: call(8); break;           \
+    case 12: call(12); break;         \
+    case 16: call(16); break;         \
+    case 20: call(20); break;         \
+    case 24: call(24); break;         \
+    case 28: call(28); break;         \
+    case 32: call(32); break;         \
+    case 48: call(48); break;         \
+    default: call(64); break;         \
+  }
+
+template <int HP>
+__device__ __forceinline__ void load_row_slice(int4 (&n)[HP / 4], float4 (&w)[HP / 4],
+                                               const int32_t* __restrict__ nbr,
+                                               const float* __restrict__ b, int64_t off,
+                                               uint64_t pol) {
+#pragma unroll
+  for (int c = 0; c < HP / 4; c++) {
+    n[c] = ld_stream_i4(reinterpret_cast<const int4*>(nbr + off) + c, pol);
+    w[c] = ld_stream_f4(reinterpret_cast<const float4*>(b + off) + c, pol);
   }
 }
 
-// The same transposed gather for the sparse positions, walking the spatial
-// tiles of the whiten sweep: a block takes one tile (a k-d in-order rank
-// range) through every level >= 1.  The children of a point are its spatial
-// neighbours in deeper levels, so their cotangents, sigmas and rows are those
-// of the same tile, about 290 KB per tile at k = 16.  One block of 1024
-// threads per SM keeps 152 tiles in flight (~45 MB, inside L2), so a row is
-// fetched from DRAM about once although each of its k entries is read by a
-// different parent; with 256-thread blocks and 8 tiles per SM the tiles in
-// flight outgrew L2 and the rows were fetched again for every parent.  The
-// entries of a position are read four at a time before their products are
-// added, in list order, so the arithmetic per position is that of
-// whiten_transpose_kernel.
-constexpr int kTransposeThreads = 1024;
-
-__device__ __forceinline__ int32_t tile_level_prefix(const int32_t* __restrict__ ts, int num_levels,
-                                                     int32_t* s_start, int32_t* s_pref,
-                                                     int32_t* s_carry, int32_t* wsum) {
-  if (threadIdx.x == 0) *s_carry = 0;
-  __syncthreads();
-  for (int base = 1; base < num_levels; base += blockDim.x) {
-    const int l = base + threadIdx.x;
-    int32_t c = 0;
-    if (l < num_levels) {
-      const int32_t a0 = ts[l];
-      c = ts[num_levels + l] - a0;
-      s_start[l] = a0;
-    }
-    int32_t x = c;
-    for (int o = 1; o < 32; o <<= 1) {
-      const int32_t y = __shfl_up_sync(0xffffffffu, x, o);
-      if ((threadIdx.x & 31) >= o) x += y;
-    }
-    if ((threadIdx.x & 31) == 31) wsum[threadIdx.x >> 5] = x;
-    __syncthreads();
-    int32_t wpre = 0;
-    for (int w = 0; w < (int)(threadIdx.x >> 5); w++) wpre += wsum[w];
-    const int32_t carry = *s_carry;
-    if (l < num_levels) s_pref[l] = carry + wpre + x - c;
-    __syncthreads();
-    if (threadIdx.x == blockDim.x - 1) *s_carry = carry + wpre + x;
-    __syncthreads();
-  }
-  return *s_carry;
-}
-
-__global__ void __launch_bounds__(kTransposeThreads, 1) whiten_transpose_tiles_kernel(
-    const int64_t* __restrict__ rowptr, const int32_t* __restrict__ cedge, int kp, int64_t n0,
-    const float* __restrict__ b, const float* __restrict__ sigma, const float* __restrict__ xibar,
-    float* __restrict__ vbar, const int32_t* __restrict__ tile_start, int64_t n_tiles,
-    int num_levels) {
-  extern __shared__ int32_t sm[];
-  int32_t* s_start = sm;              // [num_levels]
-  int32_t* s_pref = sm + num_levels;  // [num_levels + 1]
-  __shared__ int32_t s_carry;
-  __shared__ int32_t wsum[kTransposeThreads / 32];
-  for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
-    const int32_t total = tile_level_prefix(tile_start + t * num_levels, num_levels, s_start,
-                                            s_pref, &s_carry, wsum);
-    for (int32_t vi = threadIdx.x; vi < total; vi += blockDim.x) {
-      int lo = 1, hi = num_levels - 1;
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (s_pref[mid] <= vi) lo = mid; else hi = mid - 1;
-      }
-      const int64_t p = (int64_t)s_start[lo] + (vi - s_pref[lo]);
-      float acc = xibar[p] / sigma[p];
-      int64_t e = rowptr[p];
-      const int64_t e1 = rowptr[p + 1];
-      for (; e + 4 <= e1; e += 4) {
-        int32_t c[4];
-        float x[4], sg[4], w[4];
+template <int HP>
+__device__ __forceinline__ void scatter_row(float* y, const int4 (&n)[HP / 4],
+                                            const float4 (&w)[HP / 4], float a) {
+  // padded entries (weight 0, neighbour 0) add nothing and are skipped
 #pragma unroll
-        for (int q = 0; q < 4; q++) c[q] = cedge[e + q];
-#pragma unroll
-        for (int q = 0; q < 4; q++) {
-          const int64_t j = c[q] / kp + n0;
-          x[q] = xibar[j];
-          sg[q] = sigma[j];
-          w[q] = b[c[q]];
-        }
-#pragma unroll
-        for (int q = 0; q < 4; q++) acc = fmaf(-(x[q] / sg[q]), w[q], acc);
-      }
-      for (; e < e1; e++) {
-        const int32_t ce = cedge[e];
-        const int64_t j = ce / kp + n0;
-        acc = fmaf(-(xibar[j] / sigma[j]), b[ce], acc);
-      }
-      vbar[p] = acc;
-    }
-    __syncthreads();
+  for (int c = 0; c < HP / 4; c++) {
+    if (w[c].x != 0.0f) atomicAdd(y + n[c].x, w[c].x * a);
+    if (w[c].y != 0.0f) atomicAdd(y + n[c].y, w[c].y * a);
+    if (w[c].z != 0.0f) atomicAdd(y + n[c].z, w[c].z * a);
+    if (w[c].w != 0.0f) atomicAdd(y + n[c].w, w[c].w * a);
   }
 }
 
-// ---- generate VJP: reverse level sweep, deepest level first, one cooperative
-// launch with a grid barrier between levels (children of a level-l row are in
-// deeper levels, all complete once level l+1 is) ----------------------------------
-__global__ void __launch_bounds__(256) generate_adjoint_kernel(
-    const int64_t* __restrict__ rowptr, const int32_t* __restrict__ cedge, int kp, int64_t n0,
-    const float* __restrict__ b, const float* __restrict__ vbar, float* u,
-    const int64_t* __restrict__ level_off, int num_levels, LevelBarrier lb) {
+// whiten VJP, sparse rows at positions [p_begin, p_end): vbar_p += w_p and
+// vbar_c -= w_j b_j,c for every row j, w_j = xibar_j / sigma_j (for the whole
+// graph vbar's sparse entries start at 0, its dense entries at
+// L0^-T xibar_0).  No ordering between rows.
+template <int KP>
+__global__ void __launch_bounds__(256) whiten_adjoint_scatter_kernel(
+    const int32_t* __restrict__ nbr, const float* __restrict__ b, const float* __restrict__ sigma,
+    const float* __restrict__ xibar, float* vbar, int64_t n0, int64_t p_begin, int64_t p_end) {
+  constexpr int LANES = gen_lanes(KP), HP = KP / LANES, GPB = 256 / LANES;
+  const int h = threadIdx.x % LANES;
+  const uint64_t pol = l2_evict_first();
+  const int64_t stride = (int64_t)gridDim.x * GPB;
+  for (int64_t p = p_begin + (int64_t)blockIdx.x * GPB + threadIdx.x / LANES; p < p_end;
+       p += stride) {
+    int4 n[HP / 4];
+    float4 w[HP / 4];
+    load_row_slice<HP>(n, w, nbr, b, (p - n0) * KP + h * HP, pol);
+    const float a = xibar[p] / sigma[p];
+    if (h == 0) atomicAdd(vbar + p, a);
+    scatter_row<HP>(vbar, n, w, -a);
+  }
+}
+
+// generate VJP: u = (I - B)^-T vbar.  u starts as vbar; deepest level first,
+// every row i of level l -- whose u_i is complete, all its children lying in
+// deeper levels -- adds b_ia u_i at each neighbour c_a.  One cooperative
+// launch, a grid-wide barrier between levels (the barrier's release orders a
+// block's atomics before the next level's reads); the first row of a block's
+// slice is loaded before the wait.
+template <int KP>
+__global__ void __launch_bounds__(256) generate_adjoint_scatter_kernel(
+    const int32_t* __restrict__ nbr, const float* __restrict__ b, float* u,
+    const int64_t* __restrict__ level_off, int num_levels, int64_t n0, LevelBarrier lb) {
+  constexpr int LANES = gen_lanes(KP), HP = KP / LANES, GPB = 256 / LANES;
   __shared__ int s_flag;
-  const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
-  const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int h = threadIdx.x % LANES;
+  const uint64_t pol = l2_evict_first();
   const uint64_t pol_u = l2_evict_last();
   for (int l = num_levels - 1; l >= 1; l--) {
-    const int64_t hi = level_off[l + 1];
-    int64_t p = level_off[l] + gtid;
-    float acc = 0.0f;
-    int64_t e0 = 0, e1 = 0;
-    if (p < hi) {
-      acc = vbar[p];
-      e0 = rowptr[p];
-      e1 = rowptr[p + 1];
-    }
+    const int64_t lo = level_off[l], cnt = level_off[l + 1] - lo;
+    const int64_t per = (cnt + gridDim.x - 1) / gridDim.x;
+    const int64_t b0 = lo + min((int64_t)blockIdx.x * per, cnt);
+    const int64_t hi = lo + min((int64_t)(blockIdx.x + 1) * per, cnt);
+    int64_t p = b0 + threadIdx.x / LANES;
+    int4 n[HP / 4];
+    float4 w[HP / 4];
+    if (p < hi) load_row_slice<HP>(n, w, nbr, b, (p - n0) * KP + h * HP, pol);
     if (l < num_levels - 1 && lb.wait(l + 1, gridDim.x, &s_flag)) return;
     while (p < hi) {
-      for (int64_t e = e0; e < e1; e++) {
-        int32_t ce = cedge[e];
-        acc = fmaf(b[ce], ld_coherent_f(u + (ce / kp + n0), pol_u), acc);
+      const float a = ld_coherent_f(u + p, pol_u);
+      int4 nn[HP / 4];
+      float4 ww[HP / 4];
+#pragma unroll
+      for (int c = 0; c < HP / 4; c++) {
+        nn[c] = n[c];
+        ww[c] = w[c];
       }
-      st_keep_f(u + p, acc, pol_u);
-      p += gsz;
-      if (p < hi) {
-        acc = vbar[p];
-        e0 = rowptr[p];
-        e1 = rowptr[p + 1];
-      }
+      p += GPB;
+      if (p < hi) load_row_slice<HP>(n, w, nbr, b, (p - n0) * KP + h * HP, pol);
+      scatter_row<HP>(u, nn, ww, a);
     }
     __syncthreads();
     lb.arrive(l);
   }
 }
 
-// u for the dense positions, whose children are all sparse rows.
-__global__ void dense_children_kernel(const int64_t* __restrict__ rowptr,
-                                      const int32_t* __restrict__ cedge, int kp, int64_t n0,
-                                      const float* __restrict__ b, const float* __restrict__ vbar,
-                                      float* __restrict__ u) {
-  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n0;
-       p += (int64_t)gridDim.x * blockDim.x) {
-    float acc = vbar[p];
-    for (int64_t e = rowptr[p]; e < rowptr[p + 1]; e++) {
-      int32_t ce = cedge[e];
-      acc = fmaf(b[ce], u[ce / kp + n0], acc);
-    }
-    u[p] = acc;
-  }
+int whiten_adjoint_scatter(graphgp_graph_t g, graphgp_factor_t f, const float* xibar, float* vbar,
+                           int64_t p_begin, int64_t p_end, cudaStream_t s) {
+  const int64_t grid = std::min<int64_t>((p_end - p_begin + 63) / 64, (int64_t)num_sms() * 8);
+#define GGP_WSC(KP)                                                                              \
+  whiten_adjoint_scatter_kernel<KP><<<(unsigned)grid, 256, 0, s>>>(g->nbr, f->b, f->sigma, xibar, \
+                                                                   vbar, g->n0, p_begin, p_end)
+  GGP_ADJ_KP_DISPATCH(g->kp, GGP_WSC);
+#undef GGP_WSC
+  GGP_CUDA(cudaGetLastError());
+  return GRAPHGP_OK;
 }
 
 // ---- per-row factor backward ------------------------------------------------------
@@ -801,92 +733,48 @@ int dense_backward(graphgp_graph_t g, graphgp_factor_t f, const float* u0, const
 
 }  // namespace
 
-int build_child_csr(graphgp_graph_t g, cudaStream_t s) {
-  if (g->csr.rowptr) return GRAPHGP_OK;
-  int64_t rows = g->N - g->n0;
-  int64_t E = rows * g->k;
-  if (rows * g->kp >= ((int64_t)1 << 31)) return GRAPHGP_ERR_INVALID;
-  ChildCSR c;
-  GGP_TRY(g->mem.alloc(&c.rowptr, g->N + 1));
-  GGP_TRY(g->mem.alloc(&c.child, E));
-  c.edges = E;
-  Scratch sc(s);
-  if (E > 0) {
-    uint32_t *keys = nullptr, *vals = nullptr, *ks = nullptr;
-    GGP_TRY(sc.alloc(&keys, E));
-    GGP_TRY(sc.alloc(&vals, E));
-    GGP_TRY(sc.alloc(&ks, E));
-    edge_keys_kernel<<<grid_for(E, 256), 256, 0, s>>>(g->nbr, rows, g->k, g->kp, keys, vals);
-    GGP_CUDA(cudaGetLastError());
-    int bits = 0;
-    while (((int64_t)1 << bits) < g->N) bits++;
-    GGP_TRY(radix_sort_pairs(keys, vals, ks, (uint32_t*)c.child, E, bits, s));
-    rowptr_kernel<<<grid_for(E + 1, 256), 256, 0, s>>>(ks, E, g->N, c.rowptr);
-    GGP_CUDA(cudaGetLastError());
-  } else {
-    GGP_CUDA(cudaMemsetAsync(c.rowptr, 0, (g->N + 1) * sizeof(int64_t), s));
-  }
-  GGP_CUDA(cudaStreamSynchronize(s));
-  g->csr = c;
-  return GRAPHGP_OK;
-}
-
 int run_whiten_backward(graphgp_graph_t g, graphgp_factor_t f, const float* v, const float* xi,
                         const float* xibar, double logdetbar, float* vbar, double* thetabar,
                         cudaStream_t s) {
-  GGP_TRY(build_child_csr(g, s));
   int n0 = g->n0;
   // dense: vbar_0 = L0^-T xibar_0 (then children are subtracted below)
   dense_lower_tmatvec_kernel<<<(n0 + 255) / 256, 256, 0, s>>>(f->L0inv, xibar, vbar, n0);
   GGP_CUDA(cudaGetLastError());
   GGP_TRY(dense_backward(g, f, vbar, xi, -1.0f, (float)logdetbar, thetabar, s));
-  if (g->tile_start && g->num_levels <= 8192 && g->N > n0) {
-    // dense positions in position order, the sparse ones tile by tile
-    whiten_transpose_kernel<<<grid_for(n0, 256), 256, 0, s>>>(g->csr.rowptr, g->csr.child, g->kp,
-                                                              n0, f->b, f->sigma, xibar, vbar, n0);
-    GGP_CUDA(cudaGetLastError());
-    const size_t smem = (2 * (size_t)g->num_levels + 1) * sizeof(int32_t);
-    GGP_CUDA(allow_dyn_smem(whiten_transpose_tiles_kernel, smem));
-    const int64_t grid = std::min<int64_t>(g->n_tiles, num_sms());
-    whiten_transpose_tiles_kernel<<<(unsigned)grid, kTransposeThreads, smem, s>>>(
-        g->csr.rowptr, g->csr.child, g->kp, n0, f->b, f->sigma, xibar, vbar, g->tile_start,
-        g->n_tiles, g->num_levels);
-  } else {
-    whiten_transpose_kernel<<<grid_for(g->N, 256), 256, 0, s>>>(g->csr.rowptr, g->csr.child,
-                                                                g->kp, n0, f->b, f->sigma, xibar,
-                                                                vbar, g->N);
+  if (g->N > n0) {
+    GGP_CUDA(cudaMemsetAsync(vbar + n0, 0, (g->N - n0) * sizeof(float), s));
+    GGP_TRY(whiten_adjoint_scatter(g, f, xibar, vbar, n0, g->N, s));
   }
-  GGP_CUDA(cudaGetLastError());
   GGP_TRY(factor_backward(g, f, 0, xibar, (float)(2.0 * logdetbar), v, xi, nullptr, thetabar, s));
   return GRAPHGP_OK;
 }
 
 int run_generate_backward(graphgp_graph_t g, graphgp_factor_t f, const float* xi, const float* v,
                           const float* vbar, float* xibar, double* thetabar, cudaStream_t s) {
-  GGP_TRY(build_child_csr(g, s));
   float* u = g->tmp_vec;
   int n0 = g->n0;
+  GGP_CUDA(cudaMemcpyAsync(u, vbar, g->N * sizeof(float), cudaMemcpyDeviceToDevice, s));
   if (g->num_levels > 1) {
     GGP_CUDA(cudaMemsetAsync(g->level_bar, 0, g->num_levels * sizeof(uint32_t), s));
-    static int max_grid_dev[kMaxDevices] = {};
-    const int max_grid = coop_grid_cached(max_grid_dev, generate_adjoint_kernel, 256);
-    int grid = (int)std::min<int64_t>(max_grid, std::max<int64_t>((g->max_level_size + 255) / 256, 1));
     LevelBarrier lb{g->level_bar, g->err, g->max_spin};
-    const int64_t* rp = g->csr.rowptr;
-    const int32_t* ce = g->csr.child;
-    int kp = g->kp;
-    int64_t n0l = n0;
+    const int32_t* nb = g->nbr;
     const float* bw = f->b;
     const int64_t* lo = g->level_off_d;
     int nl = g->num_levels;
-    void* args[] = {(void*)&rp, (void*)&ce, (void*)&kp, (void*)&n0l, (void*)&bw, (void*)&vbar,
-                    (void*)&u,  (void*)&lo, (void*)&nl, (void*)&lb};
-    GGP_CUDA(cudaLaunchCooperativeKernel((const void*)generate_adjoint_kernel, dim3(grid),
-                                         dim3(256), args, 0, s));
+    int64_t n0l = n0;
+    void* args[] = {(void*)&nb, (void*)&bw, (void*)&u, (void*)&lo, (void*)&nl, (void*)&n0l,
+                    (void*)&lb};
+#define GGP_GSC(KP)                                                                              \
+  {                                                                                              \
+    static int max_grid_dev[kMaxDevices] = {};                                                   \
+    const int max_grid = coop_grid_cached(max_grid_dev, generate_adjoint_scatter_kernel<KP>, 256); \
+    const int grid = (int)std::min<int64_t>(max_grid, std::max<int64_t>((g->max_level_size + 63) / 64, 1)); \
+    GGP_CUDA(cudaLaunchCooperativeKernel((const void*)generate_adjoint_scatter_kernel<KP>,       \
+                                         dim3(grid), dim3(256), args, 0, s));                    \
   }
-  dense_children_kernel<<<(n0 + 255) / 256, 256, 0, s>>>(g->csr.rowptr, g->csr.child, g->kp, n0,
-                                                         f->b, vbar, u);
-  GGP_CUDA(cudaGetLastError());
+    GGP_ADJ_KP_DISPATCH(g->kp, GGP_GSC);
+#undef GGP_GSC
+  }
   // dense: xibar_0 = L0^T u_0, Lbar0 = tril(u_0 xi_0^T)
   dense_lower_tmatvec_kernel<<<(n0 + 255) / 256, 256, 0, s>>>(f->L0, u, xibar, n0);
   GGP_CUDA(cudaGetLastError());
@@ -941,22 +829,6 @@ __global__ void whiten_rows_kernel(const int32_t* __restrict__ nbr, const float*
     local += (double)out * (double)out;
   }
   if (sq) block_add_double(local, sq);
-}
-
-// Transposed gather of whiten's rows [t0, t1), scattered: vbar_i +=
-// xibar_i / sigma_i, vbar_c -= xibar_i b_ic / sigma_i (atomic adds: the
-// neighbours of a range belong to other rows and ranges).
-__global__ void whiten_rows_vjp_kernel(const int32_t* __restrict__ nbr, const float* __restrict__ b,
-                                       const float* __restrict__ sigma,
-                                       const float* __restrict__ xibar, float* vbar, int k, int kp,
-                                       int64_t n0, int64_t t0, int64_t t1) {
-  for (int64_t t = t0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < t1;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = n0 + t;
-    const float a = xibar[i] / sigma[i];
-    atomicAdd(vbar + i, a);
-    for (int e = 0; e < k; e++) atomicAdd(vbar + nbr[t * kp + e], -a * b[t * kp + e]);
-  }
 }
 
 // y[m] += sum_{i >= m} M[i][m] x[i] for the n0 x n0 lower-triangular M.
@@ -1035,9 +907,8 @@ extern "C" int graphgp_nll_backward_rows(graphgp_graph_t g, graphgp_factor_t f, 
   }
   const int64_t t0 = std::max<int64_t>(p0, n0) - n0, t1 = p1 - n0;
   if (t1 > t0) {
-    whiten_rows_vjp_kernel<<<grid_for(t1 - t0, 256), 256, 0, s>>>(g->nbr, f->b, f->sigma, xibar,
-                                                                  vbar_d, g->k, g->kp, n0, t0, t1);
-    GGP_CUDA(cudaGetLastError());
+    // the neighbours of a range belong to other rows and ranges: atomic adds
+    GGP_TRY(whiten_adjoint_scatter(g, f, xibar, vbar_d, n0 + t0, n0 + t1, s));
     GGP_TRY(factor_backward_rows(g, f, 0, xibar, (float)nllbar, v_d, xi, nullptr, thetabar_d, t0,
                                  t1, s));
   }

@@ -111,14 +111,6 @@ constexpr int kMaxK = 64;
 // Spatial tile of the whiten sweep: this many consecutive k-d in-order ranks.
 constexpr int64_t kTileR = 4096;
 
-// Children (transposed graph) in CSR form, built on first use by the
-// adjoint sweeps.
-struct ChildCSR {
-  int64_t* rowptr = nullptr;    // [N+1]
-  int32_t* child = nullptr;     // [E] entry (row * kp + slot) of the child's row
-  int64_t edges = 0;
-};
-
 }  // namespace ggp
 
 // The handle types named in graphgp.h.
@@ -148,8 +140,6 @@ struct graphgp_graph_s {
   int32_t* inorder = nullptr;
   int32_t* depth_tree = nullptr;
   int32_t* nbr_tree = nullptr;   // [(N-n0)*k]
-  // transposed graph for adjoints (lazy)
-  ggp::ChildCSR csr;
   float* tmp_vec = nullptr;      // [N] work vector for nll / adjoints
   float* tmp_vec2 = nullptr;     // [N]
 };
@@ -392,7 +382,6 @@ int dense_factor(graphgp_graph_t g, graphgp_factor_t f, const KernF& kp,
 int point_factor(graphgp_graph_t g, graphgp_factor_t f, const KernF& kp,
                  int type, cudaStream_t s);
 
-int build_child_csr(graphgp_graph_t g, cudaStream_t s);
 
 // y = M x for the n0 x n0 row-major lower-triangular M (the dense block's
 // L0 or L0^-1); adds sum y_i^2 to *sq when sq is given.

@@ -271,8 +271,6 @@ extern "C" int graphgp_server_register(graphgp_server_t sv, graphgp_graph_t g, g
   if (!sv || !g || !f || f->g != g || f->row_end >= 0 || !instance_id) return GRAPHGP_ERR_INVALID;
   std::lock_guard<std::mutex> lk(sv->mu);
   if (sv->started) return GRAPHGP_ERR_INVALID;
-  // the children CSR of the gradient requests is built now, not under capture
-  GGP_TRY(build_child_csr(g, (cudaStream_t)0));
   GGP_CUDA(cudaDeviceSynchronize());
   sv->inst.push_back(Inst{g, f, g->N, false});
   *instance_id = (int)sv->inst.size() - 1;

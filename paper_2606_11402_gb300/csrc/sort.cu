@@ -1,7 +1,6 @@
 // Device-wide exclusive scan and stable LSD radix sort of (key, value) pairs.
 // Used by the k-d tree build (per-dimension presort, Sec. 2.3 "sort-based
-// tree build"), the depth sort (Sec. 2.2 "Batch construction") and the
-// transposed graph.  Stability makes every result deterministic: equal keys
+// tree build") and the depth sort (Sec. 2.2 "Batch construction").  Stability makes every result deterministic: equal keys
 // keep their input order.
 #include "common.cuh"
 

@@ -492,6 +492,7 @@ static bool same_graph(graphgp_graph_t g, graphgp_factor_t f) {
 extern "C" int graphgp_generate(graphgp_graph_t g, graphgp_factor_t f, const float* xi_d,
                                 float* v_d, void* stream) {
   if (!same_graph(g, f) || !xi_d || !v_d) return GRAPHGP_ERR_INVALID;
+  if (xi_d < v_d + g->N && v_d < xi_d + g->N) return GRAPHGP_ERR_INVALID;  // overlap
   return run_generate(g, f, xi_d, v_d, (cudaStream_t)stream);
 }
 

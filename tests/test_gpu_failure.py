@@ -26,6 +26,23 @@ def test_bounded_wait_times_out_and_context_survives(gpu_lib):
     assert gpu_lib.selftest_wait_timeout(0) == gpu_lib.ERR_INVALID
 
 
+def test_generate_rejects_overlapping_buffers(gpu_lib):
+    """generate marks its output positions pending before the sweep, so an
+    output that overlaps the input is refused before any work."""
+    N = 5000
+    pts = torch.from_numpy(workloads.uniform_cube(N, 1)).cuda()
+    g = gpu_lib.build_graph(pts, 8)
+    f = gpu_lib.factor(g, gpu_lib.Kernel(gpu_lib.MATERN32, 1.0, 0.1, 1e-6))
+    buf = torch.from_numpy(workloads.white_noise(2 * N, 2)).cuda()
+    keep = buf.clone()
+    for a, b in [(0, 0), (0, N // 2), (N // 2, 0)]:
+        with pytest.raises(gpu_lib.GraphGPError):
+            gpu_lib.generate(g, f, buf[a:a + N], out=buf[b:b + N])
+    assert torch.equal(buf, keep)
+    v = gpu_lib.generate(g, f, buf[:N], out=buf[N:])  # adjacent, not overlapping
+    assert torch.isfinite(v).all()
+
+
 def test_server_wait_timeout_and_bad_requests(gpu_lib):
     from paper_2606_11402_gb300 import serve as sv
     pts = torch.from_numpy(workloads.unit_gaussian(200_000, 3)).cuda()
