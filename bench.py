@@ -673,7 +673,12 @@ def run_ours(args):
     adj = {"nll_ms": timed_ms(lambda: gg.nll(g, f, v, out=nll_out)),
            "nll_backward_ms": timed_ms(lambda: gg.nll_backward(g, f, v, vbar=vbar, thetabar=tbar)),
            "generate_backward_ms": timed_ms(
-               lambda: gg.generate_backward(g, f, xi, v, v, xibar=xo, thetabar=tbar))}
+               lambda: gg.generate_backward(g, f, xi, v, v, xibar=xo, thetabar=tbar)),
+           # vector cotangent only (fixed kernel: no per-row factor backward)
+           "nll_backward_vec_ms": timed_ms(
+               lambda: gg.nll_backward(g, f, v, vbar=vbar, theta=False)),
+           "generate_backward_vec_ms": timed_ms(
+               lambda: gg.generate_backward(g, f, xi, v, v, xibar=xo, theta=False))}
     for key in list(adj):
         adj[key.replace("_ms", "_points_per_s")] = N / (adj[key] / 1e3)
     diff = differentiation_bench(stream) if args.diff else None

@@ -256,6 +256,9 @@ int graphgp_nll_fused(graphgp_graph_t g, const graphgp_kernel* kern, const float
  * whiten_backward: given xibar = dL/dxi for xi = whiten(v) and a scalar
  *   logdetbar = dL/dlogdet, writes vbar_d (overwritten) and adds thetabar.
  * nll_backward: gradient of nll(v) times nllbar: vbar_d, thetabar_d.
+ * thetabar_d may be NULL: then only the vector cotangent is formed (the
+ * sweeps and scatters) and the per-row factor backward, which recomputes
+ * every row's conditional, is skipped -- the case of a fixed kernel.
  * The transposed sums (a position's cotangent from all rows that condition
  * on it) are formed with atomic adds, so vbar_d / xibar_d and thetabar_d
  * agree between calls to rounding, not bit for bit. */

@@ -413,43 +413,56 @@ def nll_noalloc(graph: Graph, fac: Factor, v: torch.Tensor, out: torch.Tensor,
     return out
 
 
-def generate_backward(graph, fac, xi, v, vbar, xibar=None, thetabar=None, stream=None):
-    """Returns (xibar, thetabar[3] += [dl, dsigma2, dnugget])."""
-    xb = torch.empty_like(xi) if xibar is None else xibar
+def _theta_arg(thetabar, theta):
+    """(tensor or None, pointer): thetabar to accumulate into, or NULL when
+    the kernel-parameter gradient is not wanted."""
+    if not theta:
+        return None, None
     tb = torch.zeros(3, dtype=torch.float64, device="cuda") if thetabar is None else thetabar
+    return tb, _dev(tb, torch.float64, 3, "thetabar")
+
+
+def generate_backward(graph, fac, xi, v, vbar, xibar=None, thetabar=None, stream=None,
+                      theta=True):
+    """Returns (xibar, thetabar[3] += [dl, dsigma2, dnugget]); with
+    theta=False the per-row factor backward is skipped and thetabar is None."""
+    xb = torch.empty_like(xi) if xibar is None else xibar
+    tb, tbp = _theta_arg(thetabar, theta)
     _check(load().graphgp_generate_backward(graph.handle, fac.handle,
                                             _dev(xi, torch.float32, graph.N, "xi"),
                                             _dev(v, torch.float32, graph.N, "v"),
                                             _dev(vbar, torch.float32, graph.N, "vbar"),
                                             _dev(xb, torch.float32, graph.N, "xibar"),
-                                            _dev(tb, torch.float64, 3, "thetabar"), _stream(stream)),
+                                            tbp, _stream(stream)),
            "generate_backward")
     return xb, tb
 
 
 def whiten_backward(graph, fac, v, xi, xibar, logdetbar=0.0, vbar=None, thetabar=None,
-                    stream=None):
-    """Returns (vbar, thetabar[3] += ...)."""
+                    stream=None, theta=True):
+    """Returns (vbar, thetabar[3] += ...); thetabar is None with theta=False."""
     vb = torch.empty_like(v) if vbar is None else vbar
-    tb = torch.zeros(3, dtype=torch.float64, device="cuda") if thetabar is None else thetabar
+    tb, tbp = _theta_arg(thetabar, theta)
     _check(load().graphgp_whiten_backward(graph.handle, fac.handle,
                                           _dev(v, torch.float32, graph.N, "v"),
                                           _dev(xi, torch.float32, graph.N, "xi"),
                                           _dev(xibar, torch.float32, graph.N, "xibar"),
                                           float(logdetbar),
                                           _dev(vb, torch.float32, graph.N, "vbar"),
-                                          _dev(tb, torch.float64, 3, "thetabar"), _stream(stream)),
+                                          tbp, _stream(stream)),
            "whiten_backward")
     return vb, tb
 
 
-def nll_backward(graph, fac, v, nllbar=1.0, vbar=None, thetabar=None, stream=None):
+def nll_backward(graph, fac, v, nllbar=1.0, vbar=None, thetabar=None, stream=None, theta=True):
+    """(nllbar dNLL/dv, thetabar[3] += nllbar dNLL/dtheta); thetabar is None
+    with theta=False."""
     vb = torch.empty_like(v) if vbar is None else vbar
-    tb = torch.zeros(3, dtype=torch.float64, device="cuda") if thetabar is None else thetabar
+    tb, tbp = _theta_arg(thetabar, theta)
     _check(load().graphgp_nll_backward(graph.handle, fac.handle,
                                        _dev(v, torch.float32, graph.N, "v"), float(nllbar),
                                        _dev(vb, torch.float32, graph.N, "vbar"),
-                                       _dev(tb, torch.float64, 3, "thetabar"), _stream(stream)),
+                                       tbp, _stream(stream)),
            "nll_backward")
     return vb, tb
 

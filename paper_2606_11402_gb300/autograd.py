@@ -31,8 +31,8 @@ def _kernel(kernel_type: int, theta: torch.Tensor) -> Kernel:
     return Kernel(int(kernel_type), float(t[1]), float(t[0]), float(t[2]))
 
 
-def _theta_grad(tb: torch.Tensor, theta: torch.Tensor) -> torch.Tensor:
-    return tb.to(device=theta.device, dtype=theta.dtype)
+def _theta_grad(tb, theta: torch.Tensor):
+    return None if tb is None else tb.to(device=theta.device, dtype=theta.dtype)
 
 
 class _Generate(torch.autograd.Function):
@@ -48,7 +48,8 @@ class _Generate(torch.autograd.Function):
     def backward(ctx, grad_v):
         xi, v, theta = ctx.saved_tensors
         xibar, tb = generate_backward(ctx.graph, ctx.fac, xi.contiguous(), v,
-                                      grad_v.contiguous().float())
+                                      grad_v.contiguous().float(),
+                                      theta=ctx.needs_input_grad[1])
         return xibar, _theta_grad(tb, theta), None, None
 
 
@@ -65,7 +66,8 @@ class _Whiten(torch.autograd.Function):
     def backward(ctx, grad_xi):
         v, xi, theta = ctx.saved_tensors
         vbar, tb = whiten_backward(ctx.graph, ctx.fac, v.contiguous(), xi,
-                                   grad_xi.contiguous().float(), 0.0)
+                                   grad_xi.contiguous().float(), 0.0,
+                                   theta=ctx.needs_input_grad[1])
         return vbar, _theta_grad(tb, theta), None, None
 
 
@@ -98,7 +100,8 @@ class _Nll(torch.autograd.Function):
     @staticmethod
     def backward(ctx, grad):
         v, theta = ctx.saved_tensors
-        vbar, tb = nll_backward(ctx.graph, ctx.fac, v.contiguous(), float(grad.item()))
+        vbar, tb = nll_backward(ctx.graph, ctx.fac, v.contiguous(), float(grad.item()),
+                                theta=ctx.needs_input_grad[1])
         return vbar, _theta_grad(tb, theta), None, None
 
 
@@ -115,7 +118,8 @@ class _NllPoints(torch.autograd.Function):
     def backward(ctx, grad):
         v, theta, points = ctx.saved_tensors
         g = float(grad.item())
-        vbar, tb = nll_backward(ctx.graph, ctx.fac, v.contiguous(), g)
+        vbar, tb = nll_backward(ctx.graph, ctx.fac, v.contiguous(), g,
+                                theta=ctx.needs_input_grad[1])
         pbar = None
         if ctx.needs_input_grad[2]:
             d = points.shape[1]

@@ -553,6 +553,13 @@ __global__ void scale_kernel(const float* __restrict__ x, float s, float* __rest
     y[i] = s * x[i];
 }
 
+__global__ void mul_kernel(const float* __restrict__ a, const float* __restrict__ x,
+                           float* __restrict__ y, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = a[i] * x[i];
+}
+
 template <int G>
 int launch_factor_backward(graphgp_graph_t g, graphgp_factor_t f, int mode, const float* coef,
                            float beta, const float* v, const float* xi, float* xibar,
@@ -740,12 +747,13 @@ int run_whiten_backward(graphgp_graph_t g, graphgp_factor_t f, const float* v, c
   // dense: vbar_0 = L0^-T xibar_0 (then children are subtracted below)
   dense_lower_tmatvec_kernel<<<(n0 + 255) / 256, 256, 0, s>>>(f->L0inv, xibar, vbar, n0);
   GGP_CUDA(cudaGetLastError());
-  GGP_TRY(dense_backward(g, f, vbar, xi, -1.0f, (float)logdetbar, thetabar, s));
+  if (thetabar) GGP_TRY(dense_backward(g, f, vbar, xi, -1.0f, (float)logdetbar, thetabar, s));
   if (g->N > n0) {
     GGP_CUDA(cudaMemsetAsync(vbar + n0, 0, (g->N - n0) * sizeof(float), s));
     GGP_TRY(whiten_adjoint_scatter(g, f, xibar, vbar, n0, g->N, s));
   }
-  GGP_TRY(factor_backward(g, f, 0, xibar, (float)(2.0 * logdetbar), v, xi, nullptr, thetabar, s));
+  if (thetabar)
+    GGP_TRY(factor_backward(g, f, 0, xibar, (float)(2.0 * logdetbar), v, xi, nullptr, thetabar, s));
   return GRAPHGP_OK;
 }
 
@@ -778,6 +786,13 @@ int run_generate_backward(graphgp_graph_t g, graphgp_factor_t f, const float* xi
   // dense: xibar_0 = L0^T u_0, Lbar0 = tril(u_0 xi_0^T)
   dense_lower_tmatvec_kernel<<<(n0 + 255) / 256, 256, 0, s>>>(f->L0, u, xibar, n0);
   GGP_CUDA(cudaGetLastError());
+  if (!thetabar) {  // vector cotangent only: xibar_i = sigma_i u_i
+    if (g->N > n0)
+      mul_kernel<<<grid_for(g->N - n0, 256), 256, 0, s>>>(f->sigma + n0, u + n0, xibar + n0,
+                                                           g->N - n0);
+    GGP_CUDA(cudaGetLastError());
+    return GRAPHGP_OK;
+  }
   GGP_TRY(dense_backward(g, f, u, xi, 1.0f, 0.0f, thetabar, s));
   GGP_TRY(factor_backward(g, f, 1, u, 0.0f, v, xi, xibar, thetabar, s));
   return GRAPHGP_OK;
@@ -923,16 +938,14 @@ static bool pair_ok(graphgp_graph_t g, graphgp_factor_t f) {
 extern "C" int graphgp_generate_backward(graphgp_graph_t g, graphgp_factor_t f, const float* xi_d,
                                          const float* v_d, const float* vbar_d, float* xibar_d,
                                          double* thetabar_d, void* stream) {
-  if (!pair_ok(g, f) || !xi_d || !v_d || !vbar_d || !xibar_d || !thetabar_d)
-    return GRAPHGP_ERR_INVALID;
+  if (!pair_ok(g, f) || !xi_d || !v_d || !vbar_d || !xibar_d) return GRAPHGP_ERR_INVALID;
   return run_generate_backward(g, f, xi_d, v_d, vbar_d, xibar_d, thetabar_d, (cudaStream_t)stream);
 }
 
 extern "C" int graphgp_whiten_backward(graphgp_graph_t g, graphgp_factor_t f, const float* v_d,
                                        const float* xi_d, const float* xibar_d, double logdetbar,
                                        float* vbar_d, double* thetabar_d, void* stream) {
-  if (!pair_ok(g, f) || !xi_d || !v_d || !xibar_d || !vbar_d || !thetabar_d)
-    return GRAPHGP_ERR_INVALID;
+  if (!pair_ok(g, f) || !xi_d || !v_d || !xibar_d || !vbar_d) return GRAPHGP_ERR_INVALID;
   return run_whiten_backward(g, f, v_d, xi_d, xibar_d, logdetbar, vbar_d, thetabar_d,
                              (cudaStream_t)stream);
 }
@@ -940,7 +953,7 @@ extern "C" int graphgp_whiten_backward(graphgp_graph_t g, graphgp_factor_t f, co
 extern "C" int graphgp_nll_backward(graphgp_graph_t g, graphgp_factor_t f, const float* v_d,
                                     double nllbar, float* vbar_d, double* thetabar_d,
                                     void* stream) {
-  if (!pair_ok(g, f) || !v_d || !vbar_d || !thetabar_d) return GRAPHGP_ERR_INVALID;
+  if (!pair_ok(g, f) || !v_d || !vbar_d) return GRAPHGP_ERR_INVALID;
   cudaStream_t s = (cudaStream_t)stream;
   float* xi = g->tmp_vec2;
   float* xibar = g->tmp_vec;

@@ -111,6 +111,26 @@ def test_thetabar_accumulates(gpu_lib):
     assert torch.allclose(t2, 2 * t1, rtol=1e-6)
 
 
+@pytest.mark.parametrize("k", [8, 16, 32])
+def test_vector_only_vjps(gpu_lib, k):
+    """theta=False passes no thetabar: the per-row factor backward is skipped
+    and the vector cotangents are those of the full call (the transposed
+    sums are atomic, so equal to rounding)."""
+    N = 3000
+    g, f, want, fo, K = _setup(gpu_lib, "gaussian", N, k, (1, 1.0, 0.1, 1e-6))
+    v = to_gpu(workloads.white_noise(N, 7))
+    xi = to_gpu(workloads.white_noise(N, 8))
+    cot = to_gpu(workloads.white_noise(N, 9))
+    for full, part in [
+            (gpu_lib.nll_backward(g, f, v), gpu_lib.nll_backward(g, f, v, theta=False)),
+            (gpu_lib.whiten_backward(g, f, v, xi, cot, 0.5),
+             gpu_lib.whiten_backward(g, f, v, xi, cot, 0.5, theta=False)),
+            (gpu_lib.generate_backward(g, f, xi, v, cot),
+             gpu_lib.generate_backward(g, f, xi, v, cot, theta=False))]:
+        assert part[1] is None
+        assert rel_norm(np_(part[0]), np_(full[0])) < 1e-6
+
+
 def _max_cond(want, K, k, rows=200):
     """Largest condition number of K_cc over sampled rows (numpy, FP64)."""
     x = want["pts_pos"].astype(np.float64)
