@@ -524,8 +524,33 @@ __global__ void __launch_bounds__(128) factor_backward_thread_kernel(
       {
         const float kaa = -ga * ba + sbar * ba * ba;
         float pl = 0.0f, ps = kaa;
+        int c = 0;
+        // four pairs per iteration, evaluated together and added in order
 #pragma unroll 1
-        for (int c = 0; c < a; c++) {
+        for (; c + 4 <= a; c += 4) {
+          float gc[4], bc[4];
+          float4 xc[4];
+#pragma unroll
+          for (int u = 0; u < 4; u++) {
+            gc[u] = sg[(c + u) * kThreadBlock];
+            bc[u] = sb[(c + u) * kThreadBlock];
+            xc[u] = st.X[(c + u) * kThreadBlock];
+          }
+          float kb[4];
+          KD kd[4];
+#pragma unroll
+          for (int u = 0; u < 4; u++) {
+            kb[u] = (-ga * bc[u] + sbar * ba * bc[u]) + (-gc[u] * ba + sbar * bc[u] * ba);
+            kd[u] = kappa_dkappa_d2<KT>(kf, sqdist(xa, xc[u]));
+          }
+#pragma unroll
+          for (int u = 0; u < 4; u++) {
+            ps += kb[u] * kd[u].k * inv_s2;
+            pl += kb[u] * kd[u].dl;
+          }
+        }
+#pragma unroll 1
+        for (; c < a; c++) {
           const float gc = sg[c * kThreadBlock], bc = sb[c * kThreadBlock];
           const float kb = (-ga * bc + sbar * ba * bc) + (-gc * ba + sbar * bc * ba);
           const KD kd = kappa_dkappa_d2<KT>(kf, sqdist(xa, st.X[c * kThreadBlock]));

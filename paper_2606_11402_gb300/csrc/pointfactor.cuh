@@ -366,14 +366,32 @@ __device__ __forceinline__ void point_factor_thread(PointRegs<K>& p, int k, cons
   const bool inc = q0.g < 0.5f * kf.s2;
   p.inc = inc;
   // gamma (increment form) or kappa (covariance form) of every pair and of
-  // every neighbour with the point, in a rolled loop
+  // every neighbour with the point, in a rolled loop taking four pairs per
+  // iteration: their coordinates are read before any value is stored, so
+  // the four evaluations overlap
 #pragma unroll 1
   for (int a = 1; a < k; a++) {
     const float4 xa = st.X[a * kThreadBlock];
+    float* ea = st.E + pair_ix(a, 0) * kThreadBlock;
+    int c = 0;
 #pragma unroll 1
-    for (int c = 0; c < a; c++) {
+    for (; c + 4 <= a; c += 4) {
+      float4 xc[4];
+#pragma unroll
+      for (int u = 0; u < 4; u++) xc[u] = st.X[(c + u) * kThreadBlock];
+      float e[4];
+#pragma unroll
+      for (int u = 0; u < 4; u++) {
+        const KG kg = kappa_gamma_d2<KT>(kf, sqdist(xa, xc[u]));
+        e[u] = inc ? kg.g : kg.k;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; u++) ea[(c + u) * kThreadBlock] = e[u];
+    }
+#pragma unroll 1
+    for (; c < a; c++) {
       const KG kg = kappa_gamma_d2<KT>(kf, sqdist(xa, st.X[c * kThreadBlock]));
-      st.E[pair_ix(a, c) * kThreadBlock] = inc ? kg.g : kg.k;
+      ea[c * kThreadBlock] = inc ? kg.g : kg.k;
     }
     const KG kq = kappa_gamma_d2<KT>(kf, sqdist(xa, xq));
     st.E[(ThreadStage<K>::kPairs + a) * kThreadBlock] = inc ? kq.g : kq.k;
