@@ -674,6 +674,9 @@ def run_ours(args):
            "nll_backward_ms": timed_ms(lambda: gg.nll_backward(g, f, v, vbar=vbar, thetabar=tbar)),
            "generate_backward_ms": timed_ms(
                lambda: gg.generate_backward(g, f, xi, v, v, xibar=xo, thetabar=tbar)),
+           # the factors recomputed: value and gradient of the NLL in one pass
+           "nll_grad_fused_ms": timed_ms(
+               lambda: gg.nll_grad_fused(g, kern, v, out=nll_out, vbar=vbar, thetabar=tbar)),
            # vector cotangent only (fixed kernel: no per-row factor backward)
            "nll_backward_vec_ms": timed_ms(
                lambda: gg.nll_backward(g, f, v, vbar=vbar, theta=False)),

@@ -247,6 +247,22 @@ int graphgp_whiten_fused(graphgp_graph_t g, const graphgp_kernel* kern, const fl
 int graphgp_nll_fused(graphgp_graph_t g, const graphgp_kernel* kern, const float* v_d,
                       double* nll_d, uint64_t* not_pd_d, void* stream);
 
+/* NLL value and gradient in one pass with the factors recomputed, never
+ * stored (Sec. 2.3 derivatives of the conditioning steps): nll_d[0] =
+ * nll(v), vbar_d = nllbar dNLL/dv (overwritten), thetabar_d += nllbar
+ * dNLL/d(lengthscale, sigma2, nugget) -- what graphgp_factor + graphgp_nll +
+ * graphgp_nll_backward return, with one computation of every row's
+ * conditional instead of two.  The form for kernel parameters that change at
+ * every step (a fit).  k <= 16 runs one pass; for 16 < k <= 32 the call
+ * builds a stored factor for its own duration (allocating it, and
+ * synchronising `stream` before freeing it).  not_pd_d as for the other
+ * on-the-fly calls.  vbar and thetabar agree with the stored-factor calls to
+ * rounding (atomic sums). */
+int graphgp_nll_grad_fused(graphgp_graph_t g, const graphgp_kernel* kern,
+                           const float* v_d, double nllbar, double* nll_d,
+                           float* vbar_d, double* thetabar_d, uint64_t* not_pd_d,
+                           void* stream);
+
 /* ---- adjoints (Sec. 2.3 "forward and backward derivatives") -------------
  * Vector-Jacobian products.  thetabar_d is double[3] =
  * [d/d lengthscale, d/d sigma2, d/d nugget] and is ACCUMULATED (+=).  The

@@ -104,6 +104,7 @@ def load() -> ctypes.CDLL:
             "graphgp_generate_fused": [_P, _P, _P, _P, _P, _P],
             "graphgp_whiten_fused": [_P, _P, _P, _P, _P, _P, _P],
             "graphgp_nll_fused": [_P, _P, _P, _P, _P, _P],
+            "graphgp_nll_grad_fused": [_P, _P, _P, ctypes.c_double, _P, _P, _P, _P, _P],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -374,6 +375,26 @@ def whiten_fused(graph: Graph, kernel: Kernel, v: torch.Tensor, out: torch.Tenso
                                        _opt(not_pd, torch.int64, 1, "not_pd"), _stream(stream)),
            "whiten_fused")
     return xi
+
+
+def nll_grad_fused(graph: Graph, kernel: Kernel, v: torch.Tensor, nllbar: float = 1.0,
+                   out: torch.Tensor | None = None, vbar: torch.Tensor | None = None,
+                   thetabar: torch.Tensor | None = None, not_pd: torch.Tensor | None = None,
+                   stream=None):
+    """graphgp_nll_grad_fused: (nll[1], vbar = nllbar dNLL/dv, thetabar[3] +=
+    nllbar dNLL/dtheta) with the factors recomputed in one pass."""
+    o = torch.empty(1, dtype=torch.float64, device="cuda") if out is None else out
+    vb = torch.empty_like(v) if vbar is None else vbar
+    tb = torch.zeros(3, dtype=torch.float64, device="cuda") if thetabar is None else thetabar
+    kc = kernel._c()
+    _check(load().graphgp_nll_grad_fused(graph.handle, ctypes.byref(kc),
+                                         _dev(v, torch.float32, graph.N, "v"), float(nllbar),
+                                         _dev(o, torch.float64, 1, "nll"),
+                                         _dev(vb, torch.float32, graph.N, "vbar"),
+                                         _dev(tb, torch.float64, 3, "thetabar"),
+                                         _opt(not_pd, torch.int64, 1, "not_pd"), _stream(stream)),
+           "nll_grad_fused")
+    return o, vb, tb
 
 
 def nll_fused(graph: Graph, kernel: Kernel, v: torch.Tensor, out: torch.Tensor | None = None,

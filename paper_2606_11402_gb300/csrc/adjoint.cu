@@ -97,6 +97,7 @@ __device__ void block_add3(double t0, double t1, double t2, double* out) {
     atomicAdd(out + 1, s1);
     atomicAdd(out + 2, s2);
   }
+  __syncthreads();  // the partials may be reused by a following call
 }
 
 // theta_bar += sum_{a,b} Kbar[a][b] dK_ab/dtheta over the dense block.
@@ -442,13 +443,101 @@ __global__ void __launch_bounds__(128) factor_backward_rescue_kernel(
   block_add3(tl, ts, tn, thetabar);
 }
 
-// The same per-row backward with one thread per point and the factor in
-// registers (k <= 16, K = padded row length), recomputed by
-// point_factor_thread: bit-identical b and sigma to the forward kernel.  Once
-// g = K_cc^-1 bbar is solved, L is dead and the coordinates are reloaded for
+// The per-row factor backward of one-thread-per-point rows, after
+// point_factor_thread left the row's factor in p and its coordinates in the
+// stage: g = K_cc^-1 (alpha v_c), then Kbar against dkappa/dtheta over the
+// pairs.  Once g is solved, L is dead and the coordinates are reloaded for
 // the kernel derivatives; the pair (a, c), c < a, takes Kbar_ac + Kbar_ca
 // against the symmetric dkappa_ac.  Each row's sum (FP32, at most k + 1
 // terms) goes straight into the thread's FP64 totals.
+template <int K, int KT>
+__device__ __forceinline__ void thread_row_backward(PointRegs<K>& p, const ThreadStage<K>& st,
+                                                    const int32_t* row_ptr, int k,
+                                                    const KernF& kf, float4 xq,
+                                                    const float* __restrict__ v, float alpha,
+                                                    float sbar, double& tl, double& ts,
+                                                    double& tn) {
+  const float inv_s2 = 1.0f / kf.s2;
+  const int4* row = reinterpret_cast<const int4*>(row_ptr);
+  float g[K];
+  int32_t ca[K];
+#pragma unroll
+  for (int q = 0; q < K / 4; q++) {
+    const int4 c = __ldg(row + q);
+    ca[4 * q] = c.x;
+    ca[4 * q + 1] = c.y;
+    ca[4 * q + 2] = c.z;
+    ca[4 * q + 3] = c.w;
+  }
+#pragma unroll
+  for (int a = 0; a < K; a++) g[a] = a < k ? alpha * v[ca[a]] : 0.0f;
+  thread_chol_solve<K>(p, k, g);
+  // b and g into the stage (the kernel values there are consumed), then a
+  // rolled loop over the pairs: row sums in FP32 (at most k + 1 terms),
+  // added to the FP64 totals
+  float* sb = st.E;
+  float* sg = st.E + K * kThreadBlock;
+#pragma unroll
+  for (int a = 0; a < K; a++) {
+    sb[a * kThreadBlock] = p.y[a];
+    sg[a * kThreadBlock] = g[a];
+  }
+  ts += sbar;  // Kbar_ii = sbar
+  tn += sbar;
+#pragma unroll 1
+  for (int a = 0; a < k; a++) {
+    const float ga = sg[a * kThreadBlock], ba = sb[a * kThreadBlock];
+    const float4 xa = st.X[a * kThreadBlock];
+    {
+      const float kaa = -ga * ba + sbar * ba * ba;
+      float pl = 0.0f, ps = kaa;
+      int c = 0;
+      // four pairs per iteration, evaluated together and added in order
+#pragma unroll 1
+      for (; c + 4 <= a; c += 4) {
+        float gc[4], bc[4];
+        float4 xc[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+          gc[u] = sg[(c + u) * kThreadBlock];
+          bc[u] = sb[(c + u) * kThreadBlock];
+          xc[u] = st.X[(c + u) * kThreadBlock];
+        }
+        float kb[4];
+        KD kd[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+          kb[u] = (-ga * bc[u] + sbar * ba * bc[u]) + (-gc[u] * ba + sbar * bc[u] * ba);
+          kd[u] = kappa_dkappa_d2<KT>(kf, sqdist(xa, xc[u]));
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+          ps += kb[u] * kd[u].k * inv_s2;
+          pl += kb[u] * kd[u].dl;
+        }
+      }
+#pragma unroll 1
+      for (; c < a; c++) {
+        const float gc = sg[c * kThreadBlock], bc = sb[c * kThreadBlock];
+        const float kb = (-ga * bc + sbar * ba * bc) + (-gc * ba + sbar * bc * ba);
+        const KD kd = kappa_dkappa_d2<KT>(kf, sqdist(xa, st.X[c * kThreadBlock]));
+        ps += kb * kd.k * inv_s2;
+        pl += kb * kd.dl;
+      }
+      const float kci = ga - 2.0f * sbar * ba;
+      const KD kq = kappa_dkappa_d2<KT>(kf, sqdist(xa, xq));
+      ps += kci * kq.k * inv_s2;
+      pl += kci * kq.dl;
+      tl += pl;
+      ts += ps;
+      tn += kaa;
+    }
+  }
+}
+
+// The same per-row backward with one thread per point and the factor in
+// registers (k <= 16, K = padded row length), recomputed by
+// point_factor_thread: bit-identical b and sigma to the forward kernel.
 template <int K, int KT>
 __global__ void __launch_bounds__(128) factor_backward_thread_kernel(
     const float4* __restrict__ xs, const int32_t* __restrict__ nbr, int64_t N, int k, int64_t n0,
@@ -460,12 +549,10 @@ __global__ void __launch_bounds__(128) factor_backward_thread_kernel(
   const ThreadStage<K> st(tstage);
   double tl = 0.0, ts = 0.0, tn = 0.0;
   const int64_t npts = N - n0;
-  const float inv_s2 = 1.0f / kf.s2;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < npts;
        t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = n0 + t;
     const int32_t* row_ptr = nbr + t * K;
-    const int4* row = reinterpret_cast<const int4*>(row_ptr);
     const float4 xq = __ldg(xs + i);
     PointRegs<K> p;
     stage_coords<K>(st, xs, row_ptr, k);
@@ -491,84 +578,100 @@ __global__ void __launch_bounds__(128) factor_backward_thread_kernel(
     const float ci = coef[i];
     const float alpha = mode == 0 ? -ci / sigma : ci;
     const float sigbar = alpha * xi[i] + beta / sigma;
-    const float sbar = sigbar / (2.0f * sigma);
-    float g[K];
-    int32_t ca[K];
-#pragma unroll
-    for (int q = 0; q < K / 4; q++) {
-      const int4 c = __ldg(row + q);
-      ca[4 * q] = c.x;
-      ca[4 * q + 1] = c.y;
-      ca[4 * q + 2] = c.z;
-      ca[4 * q + 3] = c.w;
-    }
-#pragma unroll
-    for (int a = 0; a < K; a++) g[a] = a < k ? alpha * v[ca[a]] : 0.0f;
-    thread_chol_solve<K>(p, k, g);
-    // b and g into the stage (the kernel values there are consumed), then a
-    // rolled loop over the pairs: row sums in FP32 (at most k + 1 terms),
-    // added to the FP64 totals
-    float* sb = st.E;
-    float* sg = st.E + K * kThreadBlock;
-#pragma unroll
-    for (int a = 0; a < K; a++) {
-      sb[a * kThreadBlock] = p.y[a];
-      sg[a * kThreadBlock] = g[a];
-    }
-    ts += sbar;  // Kbar_ii = sbar
-    tn += sbar;
-#pragma unroll 1
-    for (int a = 0; a < k; a++) {
-      const float ga = sg[a * kThreadBlock], ba = sb[a * kThreadBlock];
-      const float4 xa = st.X[a * kThreadBlock];
-      {
-        const float kaa = -ga * ba + sbar * ba * ba;
-        float pl = 0.0f, ps = kaa;
-        int c = 0;
-        // four pairs per iteration, evaluated together and added in order
-#pragma unroll 1
-        for (; c + 4 <= a; c += 4) {
-          float gc[4], bc[4];
-          float4 xc[4];
-#pragma unroll
-          for (int u = 0; u < 4; u++) {
-            gc[u] = sg[(c + u) * kThreadBlock];
-            bc[u] = sb[(c + u) * kThreadBlock];
-            xc[u] = st.X[(c + u) * kThreadBlock];
-          }
-          float kb[4];
-          KD kd[4];
-#pragma unroll
-          for (int u = 0; u < 4; u++) {
-            kb[u] = (-ga * bc[u] + sbar * ba * bc[u]) + (-gc[u] * ba + sbar * bc[u] * ba);
-            kd[u] = kappa_dkappa_d2<KT>(kf, sqdist(xa, xc[u]));
-          }
-#pragma unroll
-          for (int u = 0; u < 4; u++) {
-            ps += kb[u] * kd[u].k * inv_s2;
-            pl += kb[u] * kd[u].dl;
-          }
-        }
-#pragma unroll 1
-        for (; c < a; c++) {
-          const float gc = sg[c * kThreadBlock], bc = sb[c * kThreadBlock];
-          const float kb = (-ga * bc + sbar * ba * bc) + (-gc * ba + sbar * bc * ba);
-          const KD kd = kappa_dkappa_d2<KT>(kf, sqdist(xa, st.X[c * kThreadBlock]));
-          ps += kb * kd.k * inv_s2;
-          pl += kb * kd.dl;
-        }
-        const float kci = ga - 2.0f * sbar * ba;
-        const KD kq = kappa_dkappa_d2<KT>(kf, sqdist(xa, xq));
-        ps += kci * kq.k * inv_s2;
-        pl += kci * kq.dl;
-        tl += pl;
-        ts += ps;
-        tn += kaa;
-      }
-    }
+    thread_row_backward<K, KT>(p, st, row_ptr, k, kf, xq, v, alpha, sigbar / (2.0f * sigma), tl,
+                               ts, tn);
     if (mode == 1) xibar_out[i] = sigma * ci;
   }
   block_add3(tl, ts, tn, thetabar);
+}
+
+// NLL value and gradient in one pass, the factors recomputed and never stored
+// (k <= 16, one thread per point).  Each row's b and sigma come from
+// point_factor_thread with the factor kernel's FP64 rescue (warp_rescue), so
+// they are bit-identical to a stored factor's; xi_i = (v_i - b . v_c) /
+// sigma_i follows the stored sweeps' order.  The row then adds its share of
+// what graphgp_nll + graphgp_nll_backward compute: xi_i^2 and log sigma_i
+// to the value; w_i = nllbar xi_i / sigma_i at i and -w_i b_ia at each
+// neighbour (vbar, atomic adds; vbar's sparse entries start at 0); and the
+// row's factor backward with alpha = -w_i and sigbar = alpha xi_i +
+// nllbar / sigma_i (the logdet cotangent nllbar / 2, doubled).  Rows sent to
+// FP64 leave xi_i and nllbar xi_i in xi_out / xibar_out and are listed for
+// factor_backward_rescue_kernel (recomputed here when the list is full).
+// Iterations are uniform across the warp (warp_rescue is a collective).
+template <int K, int KT>
+__global__ void __launch_bounds__(128) nll_grad_fused_kernel(
+    const float4* __restrict__ xs, const int32_t* __restrict__ nbr, int64_t N, int k, int64_t n0,
+    KernF kf, float nllbar, const float* __restrict__ v, float* vbar, float* __restrict__ xi_out,
+    float* __restrict__ xibar_out, double* __restrict__ thetabar, double* __restrict__ acc,
+    unsigned long long* __restrict__ not_pd, int64_t* __restrict__ rescue_rows,
+    unsigned long long* __restrict__ rescue_count, unsigned long long rescue_cap) {
+  extern __shared__ __align__(16) unsigned char tstage[];
+  const ThreadStage<K> st(tstage);
+  double* W = fused_rescue_ws<K>(tstage);
+  const uint64_t pol_v = l2_evict_last();
+  LogAcc lacc;
+  double sq = 0.0, tl = 0.0, ts = 0.0, tn = 0.0;
+  unsigned long long clamped = 0;
+  const int64_t npts = N - n0;
+  const int64_t total = (int64_t)gridDim.x * blockDim.x;
+  const int64_t iters = (npts + total - 1) / total;  // the same on every lane
+  for (int64_t it = 0; it < iters; it++) {
+    const int64_t t = it * total + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const bool valid = t < npts;
+    const int64_t i = n0 + (valid ? t : 0);
+    const int32_t* row_ptr = nbr + (valid ? t : 0) * K;
+    const float4 xq = __ldg(xs + i);
+    PointRegs<K> p;
+    if (valid) {
+      stage_coords<K>(st, xs, row_ptr, k);
+      point_factor_thread<K, KT>(p, k, kf, st, xq);
+    }
+    const bool rescue = valid && needs_rescue(p, k, kf);
+    warp_rescue<K, KT>(p, rescue, xs, row_ptr, k, xq, kf, W);
+    if (!valid) continue;
+    const float sigma = p.sigma;
+    const float xv = (ld_keep_f(v + i, pol_v) - dot_stored_order<K, false>(p.y, row_ptr, v, pol_v)) / sigma;
+    sq += (double)xv * (double)xv;
+    lacc.mul(sigma);
+    clamped += p.clamped ? 1 : 0;
+    const float xb = nllbar * xv;
+    const float w = xb / sigma;
+    atomicAdd(vbar + i, w);
+#pragma unroll
+    for (int q = 0; q < K / 4; q++) {
+      const int4 c = __ldg(reinterpret_cast<const int4*>(row_ptr) + q);
+      if (p.y[4 * q] != 0.0f) atomicAdd(vbar + c.x, p.y[4 * q] * -w);
+      if (p.y[4 * q + 1] != 0.0f) atomicAdd(vbar + c.y, p.y[4 * q + 1] * -w);
+      if (p.y[4 * q + 2] != 0.0f) atomicAdd(vbar + c.z, p.y[4 * q + 2] * -w);
+      if (p.y[4 * q + 3] != 0.0f) atomicAdd(vbar + c.w, p.y[4 * q + 3] * -w);
+    }
+    if (rescue) {
+      xi_out[i] = xv;
+      xibar_out[i] = xb;
+      const unsigned long long slot = atomicAdd(rescue_count, 1ull);
+      if (slot < rescue_cap) {
+        rescue_rows[slot] = i;
+        continue;
+      }
+      Row64<K> R;
+      row_factor64<K, KT>(R, xs, row_ptr, k, xq, kf);
+      const float sg = (float)R.sigma;
+      const double alpha = -(double)xb / sg;
+      const double sigbar = alpha * (double)xv + (double)nllbar / sg;
+      row_backward64<K, KT>(R, xs, row_ptr, k, xq, kf, v, alpha, sigbar, sg, tl, ts, tn);
+      continue;
+    }
+    const float alpha = -xb / sigma;
+    const float sigbar = alpha * xv + nllbar / sigma;
+    thread_row_backward<K, KT>(p, st, row_ptr, k, kf, xq, v, alpha, sigbar / (2.0f * sigma), tl,
+                               ts, tn);
+  }
+  block_add3(tl, ts, tn, thetabar);
+  block_add_double(sq, acc);
+  block_add_double(lacc.log_value(), acc + 1);
+  unsigned long long c = clamped;
+  for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(not_pd, c);
 }
 
 __global__ void scale_kernel(const float* __restrict__ x, float s, float* __restrict__ y,
@@ -656,6 +759,52 @@ int launch_factor_backward_thread(graphgp_graph_t g, graphgp_factor_t f, int mod
 #undef GGP_FBT
   GGP_CUDA(cudaGetLastError());
   return GRAPHGP_OK;
+}
+
+template <int K>
+int launch_nll_grad_fused(graphgp_graph_t g, const graphgp_kernel* kern, float nllbar,
+                          const float* v, float* vbar, float* xi_tmp, float* xibar_tmp,
+                          double* thetabar, double* acc, unsigned long long* not_pd,
+                          cudaStream_t s) {
+  const int64_t npts = g->N - g->n0;
+  if (npts <= 0) return GRAPHGP_OK;
+  const unsigned grid = grid_for(npts, kThreadBlock, 8);
+  const KernF kf = make_kernf(*kern);
+  Scratch sc(s);
+  const unsigned long long cap = (unsigned long long)std::min<int64_t>(npts, kBackwardRescueMax);
+  int64_t* rows = nullptr;
+  unsigned long long* cnt = nullptr;
+  GGP_TRY(sc.alloc(&rows, cap));
+  GGP_TRY(sc.alloc(&cnt, 1));
+  GGP_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), s));
+  const unsigned rgrid = (unsigned)num_sms() * 2;
+  constexpr size_t smem = fused_smem<K>();
+#define GGP_NGF(KT)                                                                              \
+  GGP_CUDA(allow_dyn_smem(nll_grad_fused_kernel<K, KT>, smem));                                  \
+  nll_grad_fused_kernel<K, KT><<<grid, kThreadBlock, smem, s>>>(                                 \
+      g->xs, g->nbr, g->N, g->k, g->n0, kf, nllbar, v, vbar, xi_tmp, xibar_tmp, thetabar, acc,  \
+      not_pd, rows, cnt, cap);                                                                   \
+  factor_backward_rescue_kernel<K, KT><<<rgrid, 128, 0, s>>>(                                    \
+      g->xs, g->nbr, g->k, g->kp, g->n0, kf, 0, xibar_tmp, nllbar, v, xi_tmp, nullptr, thetabar, \
+      rows, cnt, cap)
+  switch (kern->type) {
+    case GRAPHGP_MATERN12: GGP_NGF(GRAPHGP_MATERN12); break;
+    case GRAPHGP_MATERN32: GGP_NGF(GRAPHGP_MATERN32); break;
+    case GRAPHGP_MATERN52: GGP_NGF(GRAPHGP_MATERN52); break;
+    default: GGP_NGF(GRAPHGP_SQEXP); break;
+  }
+#undef GGP_NGF
+  GGP_CUDA(cudaGetLastError());
+  return GRAPHGP_OK;
+}
+
+__global__ void nll_value_kernel(const double* __restrict__ acc, double* __restrict__ out) {
+  out[0] = 0.5 * acc[0] + 0.5 * acc[1];
+}
+
+__global__ void add_count_kernel(const unsigned long long* __restrict__ src,
+                                 unsigned long long* __restrict__ dst) {
+  dst[0] += src[0];
 }
 
 int launch_factor_backward_wide(graphgp_graph_t g, graphgp_factor_t f, int mode,
@@ -986,4 +1135,63 @@ extern "C" int graphgp_nll_backward(graphgp_graph_t g, graphgp_factor_t f, const
   scale_kernel<<<grid_for(g->N, 256), 256, 0, s>>>(xi, (float)nllbar, xibar, g->N);
   GGP_CUDA(cudaGetLastError());
   return run_whiten_backward(g, f, v_d, xi, xibar, 0.5 * nllbar, vbar_d, thetabar_d, s);
+}
+
+// NLL value and gradient with the factors recomputed in the pass (the
+// on-the-fly form of graphgp_nll + graphgp_nll_backward).
+extern "C" int graphgp_nll_grad_fused(graphgp_graph_t g, const graphgp_kernel* kern,
+                                      const float* v_d, double nllbar, double* nll_d,
+                                      float* vbar_d, double* thetabar_d, uint64_t* not_pd_d,
+                                      void* stream) {
+  if (!g || !valid_kernel(kern) || g->k > 32 || !v_d || !nll_d || !vbar_d || !thetabar_d)
+    return GRAPHGP_ERR_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned long long* bad = (unsigned long long*)not_pd_d;
+  if (g->kp > 16) {
+    // 16 < k <= 32: a stored factor for the duration of the call
+    graphgp_factor_t f = nullptr;
+    GGP_TRY(graphgp_factor(g, kern, stream, &f));
+    int rc = graphgp_nll(g, f, v_d, nll_d, stream);
+    if (rc == GRAPHGP_OK) rc = graphgp_nll_backward(g, f, v_d, nllbar, vbar_d, thetabar_d, stream);
+    if (rc == GRAPHGP_OK && bad) {
+      add_count_kernel<<<1, 1, 0, s>>>(f->not_pd, bad);
+      rc = cudaGetLastError() == cudaSuccess ? GRAPHGP_OK : GRAPHGP_ERR_CUDA;
+    }
+    const cudaError_t e = cudaStreamSynchronize(s);  // the factor's arrays are freed below
+    graphgp_factor_destroy(f);
+    if (rc == GRAPHGP_OK && e != cudaSuccess) rc = GRAPHGP_ERR_CUDA;
+    return rc;
+  }
+  Scratch sc(s);
+  double* acc = nullptr;  // [0] xi.xi, [1] logdet
+  GGP_TRY(sc.alloc(&acc, 2));
+  GGP_CUDA(cudaMemsetAsync(acc, 0, 16, s));
+  if (!bad) {
+    GGP_TRY(sc.alloc(&bad, 1));
+    GGP_CUDA(cudaMemsetAsync(bad, 0, 8, s));
+  }
+  const int n0 = g->n0;
+  float* xi = g->tmp_vec2;  // xi_0 and the FP64 rows' xi
+  float* xb = g->tmp_vec;   // nllbar xi for the same positions
+  graphgp_factor_s f;
+  GGP_TRY(dense_into(g, kern, sc, acc + 1, bad, f, s));
+  GGP_TRY(dense_matvec(f.L0inv, v_d, xi, n0, acc, s));
+  scale_kernel<<<(n0 + 255) / 256, 256, 0, s>>>(xi, (float)nllbar, xb, n0);
+  dense_lower_tmatvec_kernel<<<(n0 + 255) / 256, 256, 0, s>>>(f.L0inv, xb, vbar_d, n0);
+  GGP_CUDA(cudaGetLastError());
+  GGP_TRY(dense_backward(g, &f, vbar_d, xi, -1.0f, (float)(0.5 * nllbar), thetabar_d, s));
+  if (g->N > n0) {
+    GGP_CUDA(cudaMemsetAsync(vbar_d + n0, 0, (g->N - n0) * sizeof(float), s));
+    int rc = GRAPHGP_OK;
+    switch (g->kp) {
+      case 4: rc = launch_nll_grad_fused<4>(g, kern, (float)nllbar, v_d, vbar_d, xi, xb, thetabar_d, acc, bad, s); break;
+      case 8: rc = launch_nll_grad_fused<8>(g, kern, (float)nllbar, v_d, vbar_d, xi, xb, thetabar_d, acc, bad, s); break;
+      case 12: rc = launch_nll_grad_fused<12>(g, kern, (float)nllbar, v_d, vbar_d, xi, xb, thetabar_d, acc, bad, s); break;
+      default: rc = launch_nll_grad_fused<16>(g, kern, (float)nllbar, v_d, vbar_d, xi, xb, thetabar_d, acc, bad, s); break;
+    }
+    GGP_TRY(rc);
+  }
+  nll_value_kernel<<<1, 1, 0, s>>>(acc, nll_d);
+  GGP_CUDA(cudaGetLastError());
+  return GRAPHGP_OK;
 }

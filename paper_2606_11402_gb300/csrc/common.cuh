@@ -383,6 +383,14 @@ int point_factor(graphgp_graph_t g, graphgp_factor_t f, const KernF& kp,
                  int type, cudaStream_t s);
 
 
+bool valid_kernel(const graphgp_kernel* kern);
+
+// Dense block of the on-the-fly forms into a temporary handle whose arrays
+// live in the call's scratch (L0, L0^-1, sigma_0..n0-1); the block's
+// log-determinant is added to *logdet and its floored pivots to *not_pd.
+int dense_into(graphgp_graph_t g, const graphgp_kernel* kern, Scratch& sc, double* logdet,
+               unsigned long long* not_pd, graphgp_factor_s& f, cudaStream_t s);
+
 // y = M x for the n0 x n0 row-major lower-triangular M (the dense block's
 // L0 or L0^-1); adds sum y_i^2 to *sq when sq is given.
 int dense_matvec(const float* M, const float* x, float* y, int n0, double* sq, cudaStream_t s);

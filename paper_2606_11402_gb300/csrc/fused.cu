@@ -25,38 +25,6 @@
 namespace ggp {
 namespace {
 
-template <int K, bool LEVEL>
-__device__ __forceinline__ float dot_stored_order(const float (&b)[K], const int32_t* row,
-                                                  const float* v, uint64_t pol) {
-  constexpr int LANES = gen_lanes(K), HP = K / LANES;
-  float part[LANES];
-#pragma unroll
-  for (int h = 0; h < LANES; h++) {
-    float acc0 = 0.0f, acc1 = 0.0f;
-#pragma unroll
-    for (int q = 0; q < HP / 4; q++) {
-      const int e = h * HP + 4 * q;
-      const int4 c = __ldg(reinterpret_cast<const int4*>(row + e));
-      float v0, v1, v2, v3;
-      if (LEVEL) {
-        v0 = ld_level_f(v + c.x, pol); v1 = ld_level_f(v + c.y, pol);
-        v2 = ld_level_f(v + c.z, pol); v3 = ld_level_f(v + c.w, pol);
-      } else {
-        v0 = ld_keep_f(v + c.x, pol); v1 = ld_keep_f(v + c.y, pol);
-        v2 = ld_keep_f(v + c.z, pol); v3 = ld_keep_f(v + c.w, pol);
-      }
-      acc0 = fmaf(b[e], v0, acc0);
-      acc1 = fmaf(b[e + 1], v1, acc1);
-      acc0 = fmaf(b[e + 2], v2, acc0);
-      acc1 = fmaf(b[e + 3], v3, acc1);
-    }
-    part[h] = acc0 + acc1;
-  }
-  if (LANES == 4) return (part[0] + part[2]) + (part[1] + part[3]);
-  if (LANES == 2) return part[0] + part[1];
-  return part[0];
-}
-
 template <int K, int KT>
 __device__ __forceinline__ void factor_at(PointRegs<K>& p, const ThreadStage<K>& st,
                                           const float4* __restrict__ xs, const int32_t* row,
@@ -64,17 +32,6 @@ __device__ __forceinline__ void factor_at(PointRegs<K>& p, const ThreadStage<K>&
   const float4 xq = __ldg(xs + i);
   stage_coords<K>(st, xs, row, k);
   point_factor_thread<K, KT>(p, k, kf, st, xq);
-}
-
-// Dynamic shared memory of the one-thread-per-point fused kernels: the
-// staging area, then each warp's FP64 rescue workspace.
-template <int K>
-constexpr size_t fused_smem() { return ThreadStage<K>::kBytes + 4 * warp_rescue_bytes<K>(); }
-
-template <int K>
-__device__ __forceinline__ double* fused_rescue_ws(unsigned char* smem) {
-  return reinterpret_cast<double*>(smem + ThreadStage<K>::kBytes) +
-         (threadIdx.x >> 5) * (warp_rescue_bytes<K>() / sizeof(double));
 }
 
 __device__ inline void block_add_count(unsigned long long c, unsigned long long* out) {
@@ -164,6 +121,8 @@ __global__ void nll_fused_finish_kernel(const double* __restrict__ sq,
   out[0] = 0.5 * sq[0] + 0.5 * logdet[0];
 }
 
+}  // namespace
+
 bool valid_kernel(const graphgp_kernel* kern) {
   return kern && kern->type >= 0 && kern->type <= 3 && kern->sigma2 > 0 &&
          kern->lengthscale > 0 && kern->nugget >= 0 && std::isfinite(kern->rescue_tol);
@@ -184,6 +143,8 @@ int dense_into(graphgp_graph_t g, const graphgp_kernel* kern, Scratch& sc, doubl
   f.not_pd = not_pd;
   return dense_factor(g, &f, make_kernf(*kern), kern->type, s);
 }
+
+namespace {
 
 template <int K>
 int launch_whiten_fused(graphgp_graph_t g, int type, const KernF& kf, const float* v, float* xi,

@@ -65,7 +65,9 @@ struct LogAcc {
   __device__ double log_value() const { return log(m) + (double)e * 0.69314718055994530942; }
 };
 
-// Block-wide FP64 sum (blockDim.x a multiple of 32, at most 1024), added to *out.
+// Block-wide FP64 sum (blockDim.x a multiple of 32, at most 1024), added to
+// *out.  The trailing barrier lets a kernel call it again at once: the
+// shared partials are not overwritten while thread 0 still reads them.
 __device__ inline void block_add_double(double v, double* out) {
   __shared__ double red[32];
   for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -77,6 +79,7 @@ __device__ inline void block_add_double(double v, double* out) {
     for (int i = 0; i < (int)(blockDim.x >> 5); i++) s += red[i];
     atomicAdd(out, s);
   }
+  __syncthreads();
 }
 
 struct DF {  // double-float: value = hi + lo
@@ -552,6 +555,17 @@ __device__ __forceinline__ void warp_rescue(PointRegs<K>& p, bool need,
     }
     __syncwarp();
   }
+}
+
+// Dynamic shared memory of the one-thread-per-point fused kernels: the
+// staging area, then each warp's FP64 rescue workspace.
+template <int K>
+constexpr size_t fused_smem() { return ThreadStage<K>::kBytes + 4 * warp_rescue_bytes<K>(); }
+
+template <int K>
+__device__ __forceinline__ double* fused_rescue_ws(unsigned char* smem) {
+  return reinterpret_cast<double*>(smem + ThreadStage<K>::kBytes) +
+         (threadIdx.x >> 5) * (warp_rescue_bytes<K>() / sizeof(double));
 }
 
 // The FP64 conditional of the row in place of the FP32 one: b (zero past k),

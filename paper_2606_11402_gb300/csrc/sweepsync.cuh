@@ -173,6 +173,43 @@ __device__ __forceinline__ void st_stream_f(float* p, float v, uint64_t pol) {
 // entries (KP = padded row length).
 __host__ __device__ constexpr int gen_lanes(int kp) { return kp % 16 == 0 ? 4 : (kp % 8 == 0 ? 2 : 1); }
 
+// sum_a b_a v[c_a] of one row whose weights are in registers, in the stored
+// sweeps' summation order: the row cut into gen_lanes(K) slices, two
+// alternating accumulators per slice, slices combined as the sweeps'
+// xor-shuffle tree does.  LEVEL: v is being written level by level in the
+// same launch (read through ld_level_f).
+template <int K, bool LEVEL>
+__device__ __forceinline__ float dot_stored_order(const float (&b)[K], const int32_t* row,
+                                                  const float* v, uint64_t pol) {
+  constexpr int LANES = gen_lanes(K), HP = K / LANES;
+  float part[LANES];
+#pragma unroll
+  for (int h = 0; h < LANES; h++) {
+    float acc0 = 0.0f, acc1 = 0.0f;
+#pragma unroll
+    for (int q = 0; q < HP / 4; q++) {
+      const int e = h * HP + 4 * q;
+      const int4 c = __ldg(reinterpret_cast<const int4*>(row + e));
+      float v0, v1, v2, v3;
+      if (LEVEL) {
+        v0 = ld_level_f(v + c.x, pol); v1 = ld_level_f(v + c.y, pol);
+        v2 = ld_level_f(v + c.z, pol); v3 = ld_level_f(v + c.w, pol);
+      } else {
+        v0 = ld_keep_f(v + c.x, pol); v1 = ld_keep_f(v + c.y, pol);
+        v2 = ld_keep_f(v + c.z, pol); v3 = ld_keep_f(v + c.w, pol);
+      }
+      acc0 = fmaf(b[e], v0, acc0);
+      acc1 = fmaf(b[e + 1], v1, acc1);
+      acc0 = fmaf(b[e + 2], v2, acc0);
+      acc1 = fmaf(b[e + 3], v3, acc1);
+    }
+    part[h] = acc0 + acc1;
+  }
+  if (LANES == 4) return (part[0] + part[2]) + (part[1] + part[3]);
+  if (LANES == 2) return part[0] + part[1];
+  return part[0];
+}
+
 // Largest grid of kernel `fn` (block threads, dyn smem) that is co-resident.
 template <class F>
 inline int coop_grid(F fn, int threads, size_t smem = 0) {

@@ -108,3 +108,66 @@ def test_fused_differentiation_kernel_k32(gpu_lib):
     n_f = np_(gpu_lib.nll_fused(g, K, vf))[0]
     n_s = np_(gpu_lib.nll(g, f, vf))[0]
     assert abs(n_f - n_s) <= 1e-12 * abs(n_s)
+
+
+@pytest.mark.parametrize("k", [1, 5, 8, 16, 24, 32])
+@pytest.mark.parametrize("kern", KERNS)
+def test_nll_grad_fused_equals_stored(gpu_lib, k, kern):
+    """One pass with the factors recomputed (k <= 16; 16 < k <= 32 through a
+    stored factor inside the call) against factor + nll + nll_backward: the
+    value to 1e-12 relative, vbar to 1e-6, theta_bar to 1e-6 of its largest
+    component.  The per-row FP32 terms are the same expressions compiled in
+    two kernels, which may contract products into FMAs differently (one ulp
+    apart); a component that is a difference of much larger terms (sigma2
+    here, ~100x smaller than the nugget component) is held to the terms'
+    scale, not its own."""
+    N = 20_011
+    pts = workloads.cloud("gaussian", N, 70 + k)
+    g = gpu_lib.build_graph(to_gpu(pts), k, n0=max(k, 64))
+    K = gpu_lib.Kernel(*kern)
+    f = gpu_lib.factor(g, K)
+    v = gpu_lib.generate(g, f, to_gpu(workloads.white_noise(N, 71)))
+    nll_s = np_(gpu_lib.nll(g, f, v))[0]
+    vb_s, tb_s = (np_(t) for t in gpu_lib.nll_backward(g, f, v, 0.7))
+    bad = torch.zeros(1, dtype=torch.int64, device="cuda")
+    nll, vb, tb = gpu_lib.nll_grad_fused(g, K, v, 0.7, not_pd=bad)
+    assert abs(np_(nll)[0] - nll_s) <= 1e-12 * abs(nll_s)
+    assert rel_norm(np_(vb), vb_s) < 1e-6
+    assert np.all(np.abs(np_(tb) - tb_s) <= 1e-6 * np.abs(tb_s).max()), (np_(tb), tb_s)
+    _, n_bad = gpu_lib.sync_status(g, f)
+    assert int(np_(bad)[0]) == n_bad
+
+
+def test_nll_grad_fused_every_row_fp64(gpu_lib):
+    """rescue_tol < 0 sends every row to FP64.  With 2^20 + 5000 sparse rows
+    the rescue list (2^20 entries) overflows, so the last rows take the
+    in-place FP64 backward; the result still matches the stored path."""
+    N = (1 << 20) + 5064
+    pts = workloads.cloud("gaussian", N, 72)
+    g = gpu_lib.build_graph(to_gpu(pts), 16, n0=64)
+    K = gpu_lib.Kernel(1, 1.0, 0.1, 1e-6, rescue_tol=-1.0)
+    f = gpu_lib.factor(g, K)
+    v = gpu_lib.generate(g, f, to_gpu(workloads.white_noise(N, 73)))
+    nll_s = np_(gpu_lib.nll(g, f, v))[0]
+    vb_s, tb_s = (np_(t) for t in gpu_lib.nll_backward(g, f, v))
+    nll, vb, tb = gpu_lib.nll_grad_fused(g, K, v)
+    assert abs(np_(nll)[0] - nll_s) <= 1e-12 * abs(nll_s)
+    assert rel_norm(np_(vb), vb_s) < 1e-6
+    assert np.all(np.abs(np_(tb) - tb_s) <= 1e-6 * np.abs(tb_s).max()), (np_(tb), tb_s)
+
+
+def test_nll_grad_fused_against_oracle(gpu_lib):
+    N, k = 3000, 16
+    kern = (1, 1.0, 0.1, 1e-4)
+    pts = workloads.cloud("uniform", N, 74)
+    want = oracle.build_graph(pts, k, 64)
+    g = gpu_lib.build_graph(to_gpu(pts), k, n0=64)
+    fo = oracle.factor(want["pts_pos"], want["nbr_pos"], k, 64, oracle.Kernel(*kern))
+    v = oracle.generate(fo, want["nbr_pos"], k, 64,
+                        workloads.white_noise(N, 75).astype(np.float64)).astype(np.float32)
+    nll_or = oracle.nll(fo, want["nbr_pos"], k, 64, v.astype(np.float64))
+    vb_or, tb_or = oracle.nll_grad(want, oracle.Kernel(*kern), v.astype(np.float64))
+    nll, vb, tb = gpu_lib.nll_grad_fused(g, gpu_lib.Kernel(*kern), to_gpu(v))
+    assert abs(np_(nll)[0] - nll_or) <= 1e-5 * abs(nll_or)
+    assert rel_norm(np_(vb), vb_or) < 1e-4
+    assert np.all(np.abs(np_(tb) - tb_or) <= 1e-4 * np.abs(tb_or)), (np_(tb), tb_or)
