@@ -60,6 +60,10 @@ def full(pts, k, kern, n0=None, knn="brute", points=True, rescue_tol=0.0):
     vbar, tb = gg.nll_backward(g, f, to_gpu(v_in))
     out["vbar (NLL)"] = rel_norm(np_(vbar), vbar_or)
     out["theta_bar (NLL)"] = theta_rel(np_(tb), tb_or)
+    nf, vbf, tbf = gg.nll_grad_fused(g, gg.Kernel(*kern, rescue_tol=rescue_tol), to_gpu(v_in))
+    out["NLL (fused value and gradient)"] = abs(np_(nf)[0] - nll_or) / abs(nll_or)
+    out["vbar (fused value and gradient)"] = rel_norm(np_(vbf), vbar_or)
+    out["theta_bar (fused value and gradient)"] = theta_rel(np_(tbf), tb_or)
     w = np.random.default_rng(4).standard_normal(N).astype(np.float32)
     a = oracle.generate_vjp(fo, want["nbr_pos"], k, n0, xi.astype(np.float64), v_or,
                             w.astype(np.float64))
