@@ -247,6 +247,51 @@ int whiten_adjoint_scatter(graphgp_graph_t g, graphgp_factor_t f, const float* x
 }
 
 // ---- per-row factor backward ------------------------------------------------------
+// Lane a's row of Kbar against dK/dtheta for the G-lane group form, after
+// g = K_cc^-1 bbar (lane a holds g_a): Kbar_ac = -g_a b_c + sbar b_a b_c,
+// Kbar_ai = g_a - 2 sbar b_a, Kbar_ii = sbar (lane 0); the three partial
+// sums come back reduced over the group (every lane holds them).
+template <int G, int KT>
+__device__ __forceinline__ void group_row_theta(const PointState<G>& st, int a, int k, bool real,
+                                                const KernF& kf, float g, float sbar, float& pl,
+                                                float& ps, float& pn) {
+  const unsigned full = 0xffffffffu;
+  const float inv_s2 = 1.0f / kf.s2;
+  pl = ps = pn = 0.0f;
+  const float ba = st.b_own;
+#pragma unroll
+  for (int c = 0; c < G; c++) {
+    if (c >= k) break;
+    const float bc = __shfl_sync(full, st.b_own, c, G);
+    const float kb = -g * bc + sbar * ba * bc;
+    if (c == a) {
+      ps += kb;
+      pn += kb;
+    } else {
+      const KD kd = kappa_dkappa_d2<KT>(kf, st.D2[c]);
+      ps += kb * kd.k * inv_s2;
+      pl += kb * kd.dl;
+    }
+  }
+  {
+    const float kci = g - 2.0f * sbar * ba;
+    const KD kd = kappa_dkappa_d2<KT>(kf, st.d2q);
+    ps += kci * kd.k * inv_s2;
+    pl += kci * kd.dl;
+  }
+  if (!real) pl = ps = pn = 0.0f;
+  if (a == 0) {  // Kbar_ii = sbar
+    ps += sbar;
+    pn += sbar;
+  }
+#pragma unroll
+  for (int o = G / 2; o; o >>= 1) {
+    pl += __shfl_xor_sync(full, pl, o, G);
+    ps += __shfl_xor_sync(full, ps, o, G);
+    pn += __shfl_xor_sync(full, pn, o, G);
+  }
+}
+
 // mode 0 (whiten): alpha_i = -xibar_i / sigma_i, beta = 2 logdetbar.
 // mode 1 (generate): alpha_i = u_i, beta = 0; also writes xibar_i = sigma_i u_i.
 // bbar_i = alpha_i v_c(i), sigbar_i = alpha_i xi_i + beta / sigma_i.
@@ -271,7 +316,6 @@ __global__ void __launch_bounds__(128) factor_backward_kernel(
   const int64_t gid = ((int64_t)blockIdx.x * 4 + warp) * PPW + grp;
   const int64_t npts = N - n0;
   const int64_t iters = (npts + total_groups - 1) / total_groups;
-  const float inv_s2 = 1.0f / kf.s2;
   for (int64_t it = 0; it < iters; it++) {
     int64_t t = it * total_groups + gid;
     bool valid = t < npts;
@@ -291,39 +335,8 @@ __global__ void __launch_bounds__(128) factor_backward_kernel(
     float g = group_chol_solve<G>(st, a, k, bbar, Lg);
     __syncwarp();
     // row a of Kbar against dK/dtheta
-    float pl = 0.0f, ps = 0.0f, pn = 0.0f;
-    float ba = st.b_own;
-#pragma unroll
-    for (int c = 0; c < G; c++) {
-      if (c >= k) break;
-      float bc = __shfl_sync(full, st.b_own, c, G);
-      float kb = -g * bc + sbar * ba * bc;
-      if (c == a) {
-        ps += kb;
-        pn += kb;
-      } else {
-        const KD kd = kappa_dkappa_d2<KT>(kf, st.D2[c]);
-        ps += kb * kd.k * inv_s2;
-        pl += kb * kd.dl;
-      }
-    }
-    {
-      float kci = g - 2.0f * sbar * ba;
-      const KD kd = kappa_dkappa_d2<KT>(kf, st.d2q);
-      ps += kci * kd.k * inv_s2;
-      pl += kci * kd.dl;
-    }
-    if (!real) pl = ps = pn = 0.0f;
-    if (a == 0) {  // Kbar_ii = sbar
-      ps += sbar;
-      pn += sbar;
-    }
-#pragma unroll
-    for (int o = G / 2; o; o >>= 1) {
-      pl += __shfl_xor_sync(full, pl, o, G);
-      ps += __shfl_xor_sync(full, ps, o, G);
-      pn += __shfl_xor_sync(full, pn, o, G);
-    }
+    float pl, ps, pn;
+    group_row_theta<G, KT>(st, a, k, real, kf, g, sbar, pl, ps, pn);
     // rows the forward factor recomputed in FP64 (rescue.cuh): the FP32 sums
     // above are discarded and the row goes to factor_backward_rescue_kernel
     const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (grp * G));
@@ -674,6 +687,107 @@ __global__ void __launch_bounds__(128) nll_grad_fused_kernel(
   if ((threadIdx.x & 31) == 0 && c) atomicAdd(not_pd, c);
 }
 
+// The FP64 conditional of a warp's row out of line: the rescue is rare, and
+// inlined its state would raise the register count of the whole kernel.
+template <int KT>
+__device__ __noinline__ WarpRow64 warp_row_factor64_outlined(const float4* __restrict__ xs,
+                                                            const int32_t* row, int k,
+                                                            float4 xq, KernF kf, double* W) {
+  return warp_row_factor64<32, KT>(xs, row, k, xq, kf, W);
+}
+
+// The one-pass NLL value and gradient for 16 < k <= 32: one warp per point,
+// the 32-lane group factor (point_factor_group with the factor kernel's
+// rescue decision), so b and sigma are the stored factor's; a row that needs
+// FP64 takes its b and sigma from warp_row_factor64 for the value and the
+// scatter and is listed for factor_backward_rescue_kernel (the list holds
+// every row); the other rows run the group backward (group_chol_solve,
+// group_row_theta) on the factor still in the warp's shared memory.
+template <int KP, int KT>
+__global__ void __launch_bounds__(128, 3) nll_grad_fused_group_kernel(
+    const float4* __restrict__ xs, const int32_t* __restrict__ nbr, int64_t N, int k, int64_t n0,
+    KernF kf, float nllbar, const float* __restrict__ v, float* vbar, float* __restrict__ xi_out,
+    float* __restrict__ xibar_out, double* __restrict__ thetabar, double* __restrict__ acc,
+    unsigned long long* __restrict__ not_pd, int64_t* __restrict__ rescue_rows,
+    unsigned long long* __restrict__ rescue_count) {
+  constexpr int GS = PFLayout<32>::GS;
+  __shared__ __align__(16) float Ls[4 * GS];
+  extern __shared__ __align__(16) double gws[];  // 4 x 32 x 33 doubles (FP64 rescue)
+  const int a = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned full = 0xffffffffu;
+  float* Lg = Ls + warp * GS;
+  double* W = gws + warp * (32 * 33);
+  const uint64_t pol_v = l2_evict_last();
+  LogAcc lacc;
+  double sq = 0.0, tl = 0.0, ts = 0.0, tn = 0.0;
+  unsigned long long clamped = 0;
+  const int64_t npts = N - n0;
+  const int64_t nw = (int64_t)gridDim.x * 4;
+  for (int64_t t = (int64_t)blockIdx.x * 4 + warp; t < npts; t += nw) {  // warp-uniform
+    const int64_t i = n0 + t;
+    const int32_t* row = nbr + t * KP;
+    const bool real = a < k;
+    const int32_t ca = real ? __ldg(row + a) : 0;
+    const float4 xq = __ldg(xs + i);
+    PointState<32> st;
+    point_factor_group<32, KT>(st, a, k, kf, __ldg(xs + ca), xq, Lg);
+    __syncwarp();
+    const bool lane_bad = real && !isfinite(st.b_own);
+    const bool rescue = st.clamped || row_error_too_large(st.max_ratio, st.varw, st.sigma, kf) ||
+                        !isfinite(st.sigma) || __ballot_sync(full, lane_bad);
+    float b = real ? st.b_own : 0.0f, sigma = st.sigma;
+    bool clamp = st.clamped;
+    if (rescue) {
+      const WarpRow64 w = warp_row_factor64_outlined<KT>(xs, row, k, xq, kf, W);
+      b = real ? (float)w.b : 0.0f;
+      sigma = (float)w.sigma;
+      clamp = w.clamped;
+    }
+    const float dot = warp_dot_stored_order<KP, false>(b, row, v, pol_v);
+    float xv = 0.0f;
+    if (a == 0) xv = (ld_keep_f(v + i, pol_v) - dot) / sigma;
+    xv = __shfl_sync(full, xv, 0);
+    const float xb = nllbar * xv;
+    const float w = xb / sigma;
+    if (a == 0) {
+      sq += (double)xv * (double)xv;
+      lacc.mul(sigma);
+      clamped += clamp ? 1 : 0;
+      atomicAdd(vbar + i, w);
+    }
+    if (real && b != 0.0f) atomicAdd(vbar + ca, b * -w);
+    if (rescue) {
+      if (a == 0) {
+        xi_out[i] = xv;
+        xibar_out[i] = xb;
+        rescue_rows[atomicAdd(rescue_count, 1ull)] = i;
+      }
+      __syncwarp();
+      continue;
+    }
+    const float alpha = -xb / sigma;
+    const float sigbar = alpha * xv + nllbar / sigma;
+    const float sbar = sigbar / (2.0f * sigma);
+    const float bbar = real ? alpha * v[ca] : 0.0f;
+    const float g = group_chol_solve<32>(st, a, k, bbar, Lg);
+    __syncwarp();
+    float pl, ps, pn;
+    group_row_theta<32, KT>(st, a, k, real, kf, g, sbar, pl, ps, pn);
+    if (a == 0) {
+      tl += pl;
+      ts += ps;
+      tn += pn;
+    }
+    __syncwarp();
+  }
+  block_add3(tl, ts, tn, thetabar);
+  block_add_double(sq, acc);
+  block_add_double(a == 0 ? lacc.log_value() : 0.0, acc + 1);
+  unsigned long long c = clamped;
+  for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(full, c, o);
+  if (a == 0 && c) atomicAdd(not_pd, c);
+}
+
 __global__ void scale_kernel(const float* __restrict__ x, float s, float* __restrict__ y,
                              int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -798,13 +912,45 @@ int launch_nll_grad_fused(graphgp_graph_t g, const graphgp_kernel* kern, float n
   return GRAPHGP_OK;
 }
 
-__global__ void nll_value_kernel(const double* __restrict__ acc, double* __restrict__ out) {
-  out[0] = 0.5 * acc[0] + 0.5 * acc[1];
+template <int KP>
+int launch_nll_grad_fused_group(graphgp_graph_t g, const graphgp_kernel* kern, float nllbar,
+                                const float* v, float* vbar, float* xi_tmp, float* xibar_tmp,
+                                double* thetabar, double* acc, unsigned long long* not_pd,
+                                cudaStream_t s) {
+  const int64_t npts = g->N - g->n0;
+  if (npts <= 0) return GRAPHGP_OK;
+  const unsigned grid = grid_for((npts + 3) / 4 * 128, 128, 16);
+  const KernF kf = make_kernf(*kern);
+  Scratch sc(s);
+  int64_t* rows = nullptr;
+  unsigned long long* cnt = nullptr;
+  GGP_TRY(sc.alloc(&rows, npts));
+  GGP_TRY(sc.alloc(&cnt, 1));
+  GGP_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), s));
+  const unsigned rgrid = (unsigned)num_sms() * 2;
+  constexpr size_t smem = (size_t)4 * 32 * 33 * sizeof(double);
+#define GGP_NGG(KT)                                                                              \
+  GGP_CUDA(cudaFuncSetAttribute(nll_grad_fused_group_kernel<KP, KT>,                            \
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));        \
+  nll_grad_fused_group_kernel<KP, KT><<<grid, 128, smem, s>>>(                                   \
+      g->xs, g->nbr, g->N, g->k, g->n0, kf, nllbar, v, vbar, xi_tmp, xibar_tmp, thetabar, acc,  \
+      not_pd, rows, cnt);                                                                        \
+  factor_backward_rescue_kernel<32, KT><<<rgrid, 128, 0, s>>>(                                   \
+      g->xs, g->nbr, g->k, g->kp, g->n0, kf, 0, xibar_tmp, nllbar, v, xi_tmp, nullptr, thetabar, \
+      rows, cnt, (unsigned long long)npts)
+  switch (kern->type) {
+    case GRAPHGP_MATERN12: GGP_NGG(GRAPHGP_MATERN12); break;
+    case GRAPHGP_MATERN32: GGP_NGG(GRAPHGP_MATERN32); break;
+    case GRAPHGP_MATERN52: GGP_NGG(GRAPHGP_MATERN52); break;
+    default: GGP_NGG(GRAPHGP_SQEXP); break;
+  }
+#undef GGP_NGG
+  GGP_CUDA(cudaGetLastError());
+  return GRAPHGP_OK;
 }
 
-__global__ void add_count_kernel(const unsigned long long* __restrict__ src,
-                                 unsigned long long* __restrict__ dst) {
-  dst[0] += src[0];
+__global__ void nll_value_kernel(const double* __restrict__ acc, double* __restrict__ out) {
+  out[0] = 0.5 * acc[0] + 0.5 * acc[1];
 }
 
 int launch_factor_backward_wide(graphgp_graph_t g, graphgp_factor_t f, int mode,
@@ -1147,21 +1293,6 @@ extern "C" int graphgp_nll_grad_fused(graphgp_graph_t g, const graphgp_kernel* k
     return GRAPHGP_ERR_INVALID;
   cudaStream_t s = (cudaStream_t)stream;
   unsigned long long* bad = (unsigned long long*)not_pd_d;
-  if (g->kp > 16) {
-    // 16 < k <= 32: a stored factor for the duration of the call
-    graphgp_factor_t f = nullptr;
-    GGP_TRY(graphgp_factor(g, kern, stream, &f));
-    int rc = graphgp_nll(g, f, v_d, nll_d, stream);
-    if (rc == GRAPHGP_OK) rc = graphgp_nll_backward(g, f, v_d, nllbar, vbar_d, thetabar_d, stream);
-    if (rc == GRAPHGP_OK && bad) {
-      add_count_kernel<<<1, 1, 0, s>>>(f->not_pd, bad);
-      rc = cudaGetLastError() == cudaSuccess ? GRAPHGP_OK : GRAPHGP_ERR_CUDA;
-    }
-    const cudaError_t e = cudaStreamSynchronize(s);  // the factor's arrays are freed below
-    graphgp_factor_destroy(f);
-    if (rc == GRAPHGP_OK && e != cudaSuccess) rc = GRAPHGP_ERR_CUDA;
-    return rc;
-  }
   Scratch sc(s);
   double* acc = nullptr;  // [0] xi.xi, [1] logdet
   GGP_TRY(sc.alloc(&acc, 2));
@@ -1187,7 +1318,11 @@ extern "C" int graphgp_nll_grad_fused(graphgp_graph_t g, const graphgp_kernel* k
       case 4: rc = launch_nll_grad_fused<4>(g, kern, (float)nllbar, v_d, vbar_d, xi, xb, thetabar_d, acc, bad, s); break;
       case 8: rc = launch_nll_grad_fused<8>(g, kern, (float)nllbar, v_d, vbar_d, xi, xb, thetabar_d, acc, bad, s); break;
       case 12: rc = launch_nll_grad_fused<12>(g, kern, (float)nllbar, v_d, vbar_d, xi, xb, thetabar_d, acc, bad, s); break;
-      default: rc = launch_nll_grad_fused<16>(g, kern, (float)nllbar, v_d, vbar_d, xi, xb, thetabar_d, acc, bad, s); break;
+      case 16: rc = launch_nll_grad_fused<16>(g, kern, (float)nllbar, v_d, vbar_d, xi, xb, thetabar_d, acc, bad, s); break;
+      case 20: rc = launch_nll_grad_fused_group<20>(g, kern, (float)nllbar, v_d, vbar_d, xi, xb, thetabar_d, acc, bad, s); break;
+      case 24: rc = launch_nll_grad_fused_group<24>(g, kern, (float)nllbar, v_d, vbar_d, xi, xb, thetabar_d, acc, bad, s); break;
+      case 28: rc = launch_nll_grad_fused_group<28>(g, kern, (float)nllbar, v_d, vbar_d, xi, xb, thetabar_d, acc, bad, s); break;
+      default: rc = launch_nll_grad_fused_group<32>(g, kern, (float)nllbar, v_d, vbar_d, xi, xb, thetabar_d, acc, bad, s); break;
     }
     GGP_TRY(rc);
   }

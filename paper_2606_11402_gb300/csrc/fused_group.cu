@@ -55,40 +55,6 @@ __device__ __forceinline__ WarpFactor warp_factor(const float4* __restrict__ xs,
   return out;
 }
 
-// sum_e b_e v[c_e] in the stored sweeps' order, valid on lane 0.
-template <int KP, bool LEVEL>
-__device__ __forceinline__ float warp_dot_stored_order(float b_own, const int32_t* row,
-                                                       const float* v, uint64_t pol) {
-  constexpr int LANES = gen_lanes(KP), HP = KP / LANES;
-  const int h = (threadIdx.x & 31) % LANES;
-  float acc0 = 0.0f, acc1 = 0.0f;
-#pragma unroll
-  for (int q = 0; q < HP / 4; q++) {
-    const int e = h * HP + 4 * q;
-    const int4 c = __ldg(reinterpret_cast<const int4*>(row + e));
-    const float w0 = __shfl_sync(0xffffffffu, b_own, (e + 0) & 31);
-    const float w1 = __shfl_sync(0xffffffffu, b_own, (e + 1) & 31);
-    const float w2 = __shfl_sync(0xffffffffu, b_own, (e + 2) & 31);
-    const float w3 = __shfl_sync(0xffffffffu, b_own, (e + 3) & 31);
-    float v0, v1, v2, v3;
-    if (LEVEL) {
-      v0 = ld_level_f(v + c.x, pol); v1 = ld_level_f(v + c.y, pol);
-      v2 = ld_level_f(v + c.z, pol); v3 = ld_level_f(v + c.w, pol);
-    } else {
-      v0 = ld_keep_f(v + c.x, pol); v1 = ld_keep_f(v + c.y, pol);
-      v2 = ld_keep_f(v + c.z, pol); v3 = ld_keep_f(v + c.w, pol);
-    }
-    acc0 = fmaf(w0, v0, acc0);
-    acc1 = fmaf(w1, v1, acc1);
-    acc0 = fmaf(w2, v2, acc0);
-    acc1 = fmaf(w3, v3, acc1);
-  }
-  float acc = acc0 + acc1;
-  if (LANES >= 4) acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-  if (LANES >= 2) acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-  return acc;
-}
-
 __device__ inline void block_count(unsigned long long c, unsigned long long* out) {
   for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
   if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);

@@ -210,6 +210,42 @@ __device__ __forceinline__ float dot_stored_order(const float (&b)[K], const int
   return part[0];
 }
 
+// The same sum for the one-warp-per-point form: lane a holds b_a (b_own);
+// lane h of the warp forms slice h from the shuffled weights and the row's
+// neighbour indices (padding entries included).  Valid on lane 0.
+template <int KP, bool LEVEL>
+__device__ __forceinline__ float warp_dot_stored_order(float b_own, const int32_t* row,
+                                                       const float* v, uint64_t pol) {
+  constexpr int LANES = gen_lanes(KP), HP = KP / LANES;
+  const int h = (threadIdx.x & 31) % LANES;
+  float acc0 = 0.0f, acc1 = 0.0f;
+#pragma unroll
+  for (int q = 0; q < HP / 4; q++) {
+    const int e = h * HP + 4 * q;
+    const int4 c = __ldg(reinterpret_cast<const int4*>(row + e));
+    const float w0 = __shfl_sync(0xffffffffu, b_own, (e + 0) & 31);
+    const float w1 = __shfl_sync(0xffffffffu, b_own, (e + 1) & 31);
+    const float w2 = __shfl_sync(0xffffffffu, b_own, (e + 2) & 31);
+    const float w3 = __shfl_sync(0xffffffffu, b_own, (e + 3) & 31);
+    float v0, v1, v2, v3;
+    if (LEVEL) {
+      v0 = ld_level_f(v + c.x, pol); v1 = ld_level_f(v + c.y, pol);
+      v2 = ld_level_f(v + c.z, pol); v3 = ld_level_f(v + c.w, pol);
+    } else {
+      v0 = ld_keep_f(v + c.x, pol); v1 = ld_keep_f(v + c.y, pol);
+      v2 = ld_keep_f(v + c.z, pol); v3 = ld_keep_f(v + c.w, pol);
+    }
+    acc0 = fmaf(w0, v0, acc0);
+    acc1 = fmaf(w1, v1, acc1);
+    acc0 = fmaf(w2, v2, acc0);
+    acc1 = fmaf(w3, v3, acc1);
+  }
+  float acc = acc0 + acc1;
+  if (LANES >= 4) acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+  if (LANES >= 2) acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+  return acc;
+}
+
 // Largest grid of kernel `fn` (block threads, dyn smem) that is co-resident.
 template <class F>
 inline int coop_grid(F fn, int threads, size_t smem = 0) {

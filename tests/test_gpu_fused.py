@@ -138,13 +138,15 @@ def test_nll_grad_fused_equals_stored(gpu_lib, k, kern):
     assert int(np_(bad)[0]) == n_bad
 
 
-def test_nll_grad_fused_every_row_fp64(gpu_lib):
-    """rescue_tol < 0 sends every row to FP64.  With 2^20 + 5000 sparse rows
-    the rescue list (2^20 entries) overflows, so the last rows take the
-    in-place FP64 backward; the result still matches the stored path."""
-    N = (1 << 20) + 5064
+@pytest.mark.parametrize("k,N", [(16, (1 << 20) + 5064), (32, 6000)])
+def test_nll_grad_fused_every_row_fp64(gpu_lib, k, N):
+    """rescue_tol < 0 sends every row to FP64.  k = 16 with 2^20 + 5000
+    sparse rows: the rescue list (2^20 entries) overflows, so the last rows
+    take the in-place FP64 backward.  k = 32: every row's value and scatter
+    use the warp's FP64 factor and its backward is listed.  The result still
+    matches the stored path."""
     pts = workloads.cloud("gaussian", N, 72)
-    g = gpu_lib.build_graph(to_gpu(pts), 16, n0=64)
+    g = gpu_lib.build_graph(to_gpu(pts), k, n0=64)
     K = gpu_lib.Kernel(1, 1.0, 0.1, 1e-6, rescue_tol=-1.0)
     f = gpu_lib.factor(g, K)
     v = gpu_lib.generate(g, f, to_gpu(workloads.white_noise(N, 73)))
@@ -156,9 +158,11 @@ def test_nll_grad_fused_every_row_fp64(gpu_lib):
     assert np.all(np.abs(np_(tb) - tb_s) <= 1e-6 * np.abs(tb_s).max()), (np_(tb), tb_s)
 
 
-def test_nll_grad_fused_against_oracle(gpu_lib):
-    N, k = 3000, 16
-    kern = (1, 1.0, 0.1, 1e-4)
+@pytest.mark.parametrize("k,kern", [(16, (1, 1.0, 0.1, 1e-4)), (32, (3, 1.0, 0.03, 1e-4))])
+def test_nll_grad_fused_against_oracle(gpu_lib, k, kern):
+    """Thread form (k = 16) and 32-lane group form (k = 32, the
+    differentiation kernel) against the oracle's closed-form gradient."""
+    N = 3000
     pts = workloads.cloud("uniform", N, 74)
     want = oracle.build_graph(pts, k, 64)
     g = gpu_lib.build_graph(to_gpu(pts), k, n0=64)
