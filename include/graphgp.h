@@ -253,11 +253,11 @@ int graphgp_nll_fused(graphgp_graph_t g, const graphgp_kernel* kern, const float
  * dNLL/d(lengthscale, sigma2, nugget) -- what graphgp_factor + graphgp_nll +
  * graphgp_nll_backward return, with one computation of every row's
  * conditional instead of two.  The form for kernel parameters that change at
- * every step (a fit).  k <= 16 runs one pass; for 16 < k <= 32 the call
- * builds a stored factor for its own duration (allocating it, and
- * synchronising `stream` before freeing it).  not_pd_d as for the other
- * on-the-fly calls.  vbar and thetabar agree with the stored-factor calls to
- * rounding (atomic sums). */
+ * every step (a fit).  k <= 32 (one thread per point for k <= 16, one warp
+ * per point above); each call allocates stream-ordered scratch for the dense
+ * block and the FP64 rescue list.  not_pd_d as for the other on-the-fly
+ * calls.  vbar and thetabar agree with the stored-factor calls to rounding
+ * (atomic sums). */
 int graphgp_nll_grad_fused(graphgp_graph_t g, const graphgp_kernel* kern,
                            const float* v_d, double nllbar, double* nll_d,
                            float* vbar_d, double* thetabar_d, uint64_t* not_pd_d,
