@@ -77,6 +77,33 @@ def _measured_traffic(kernel: str, N: int):
     return traffic
 
 
+def _cpulist(text):
+    out = set()
+    for part in text.strip().split(","):
+        if not part:
+            continue
+        lo, _, hi = part.partition("-")
+        out.update(range(int(lo), int(hi or lo) + 1))
+    return out
+
+
+def _near_gpu_cpus(dev):
+    """Host cores of the GPU's NUMA node (sysfs local_cpulist of its PCI
+    address) among those this process may use, or None where the topology is
+    not exposed or every usable core is already local."""
+    import torch
+    try:
+        p = torch.cuda.get_device_properties(dev)
+        addr = "%04x:%02x:%02x.0" % (p.pci_domain_id, p.pci_bus_id, p.pci_device_id)
+        with open(f"/sys/bus/pci/devices/{addr}/local_cpulist") as fh:
+            cpus = _cpulist(fh.read())
+        avail = os.sched_getaffinity(0)
+        cpus &= avail
+        return cpus if cpus and cpus != avail else None
+    except Exception:
+        return None
+
+
 def _clock_sampler(out_path):
     q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -594,10 +621,18 @@ def run_ours(args):
     # the neighbouring steps (device vectors double-buffered; a buffer is
     # reused only after the copies that read it have finished).
     s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+    # the pinned buffers are allocated from the host cores nearest the GPU, so
+    # their pages sit in the GPU's local memory node (affinity restored after)
+    near = _near_gpu_cpus(local)
+    all_cpus = os.sched_getaffinity(0)
+    if near:
+        os.sched_setaffinity(0, near)
     xi_pin = torch.from_numpy(xi_h).pin_memory()
     v_pin = [torch.empty(N, dtype=torch.float32).pin_memory() for _ in range(2)]
     xo_pin = [torch.empty(N, dtype=torch.float32).pin_memory() for _ in range(2)]
     ld_pin = [torch.empty(1, dtype=torch.float64).pin_memory() for _ in range(2)]
+    if near:
+        os.sched_setaffinity(0, all_cpus)
     xi_d = [torch.empty_like(xi) for _ in range(2)]
     v_d, xo_d, ld_d = [v, torch.empty_like(v)], [xo, torch.empty_like(xo)], [ld, torch.empty_like(ld)]
     gen_done, out_done = [None, None], [None, None]
@@ -734,7 +769,9 @@ def run_ours(args):
                    "not_pd_rows": nbad, "fused": fused, "adjoints": adj},
         "e2e": {"value": e2e_value, "unit": UNIT, "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": 4 * N, "d2h_bytes_per_step": 8 * N + 8,
-                "copies": "pinned host buffers, own streams, overlapping neighbouring steps"},
+                "copies": "pinned host buffers, own streams, overlapping neighbouring steps",
+                "host_buffers": ("allocated from the %d host cores local to the GPU" % len(near))
+                if near else "allocated without a NUMA preference"},
         # per step: generate = dense mat-vec + the two single-block runs of
         # small levels + the cooperative level sweep; whiten = dense mat-vec +
         # tile sweep; logdet is a device-to-device copy of the factor's sum
