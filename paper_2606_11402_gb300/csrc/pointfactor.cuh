@@ -568,18 +568,4 @@ __device__ __forceinline__ double* fused_rescue_ws(unsigned char* smem) {
          (threadIdx.x >> 5) * (warp_rescue_bytes<K>() / sizeof(double));
 }
 
-// The FP64 conditional of the row in place of the FP32 one: b (zero past k),
-// sigma and the floor flag, rounded to FP32.
-template <int K, int KT>
-__device__ __forceinline__ void rescue_thread(PointRegs<K>& p, const float4* __restrict__ xs,
-                                              const int32_t* row, int k, float4 xq,
-                                              const KernF& kf) {
-  Row64<K> R;
-  row_factor64<K, KT>(R, xs, row, k, xq, kf);
-#pragma unroll
-  for (int a = 0; a < K; a++) p.y[a] = a < k ? (float)R.b[a] : 0.0f;
-  p.sigma = (float)R.sigma;
-  p.clamped = R.clamped;
-}
-
 }  // namespace ggp
