@@ -12,6 +12,7 @@ graphgp_factor call) unless a Factor is passed in.
     ld  = logdet(graph, kernel_type, theta)            # log det L L^T
     nll = nll(graph, kernel_type, theta, v)            # 0.5 xi.xi + 0.5 ld
     nll = nll(graph, kernel_type, theta, v, points)    # also d/d points
+    nll = nll_fit(graph, kernel_type, theta, v)        # one pass (k <= 32)
 
 With `points` (the [N, d] tensor the graph was built from; its values are
 not read again) the NLL is also differentiable with respect to the point
@@ -22,7 +23,7 @@ from __future__ import annotations
 import torch
 
 from . import (Factor, Graph, Kernel, factor as _factor, generate_backward, logdet as _logdet,
-               nll as _nll, nll_backward, nll_backward_points, whiten_backward,
+               nll as _nll, nll_backward, nll_backward_points, nll_grad_fused, whiten_backward,
                generate as _generate, whiten as _whiten)
 
 
@@ -128,6 +129,24 @@ class _NllPoints(torch.autograd.Function):
         return vbar, _theta_grad(tb, theta), pbar, None, None
 
 
+class _NllFit(torch.autograd.Function):
+    """The NLL of a fit step: value and gradient come from one pass with the
+    factors recomputed (graphgp_nll_grad_fused), so backward only scales the
+    stored gradient by the incoming cotangent."""
+
+    @staticmethod
+    def forward(ctx, v, theta, graph, kernel_type):
+        out, vbar, tb = nll_grad_fused(graph, _kernel(kernel_type, theta), v.contiguous())
+        ctx.save_for_backward(vbar, _theta_grad(tb, theta))
+        return out.reshape(())
+
+    @staticmethod
+    def backward(ctx, grad):
+        vbar, tb = ctx.saved_tensors
+        return (vbar * grad.to(device=vbar.device, dtype=vbar.dtype),
+                tb * grad.to(device=tb.device, dtype=tb.dtype), None, None)
+
+
 def generate(graph: Graph, kernel_type: int, theta: torch.Tensor, xi: torch.Tensor):
     return _Generate.apply(xi, theta, graph, kernel_type)
 
@@ -147,3 +166,9 @@ def nll(graph: Graph, kernel_type: int, theta: torch.Tensor, v: torch.Tensor,
     if points.shape != (graph.N, points.shape[1]) or not 1 <= points.shape[1] <= 3:
         raise ValueError("points must be the [N, d] tensor the graph was built from")
     return _NllPoints.apply(v, theta, points, graph, kernel_type)
+
+
+def nll_fit(graph: Graph, kernel_type: int, theta: torch.Tensor, v: torch.Tensor):
+    """nll() for a fit (k <= 32): the gradient with respect to v and theta is
+    computed in the same pass as the value, each conditional once."""
+    return _NllFit.apply(v, theta, graph, kernel_type)

@@ -199,6 +199,33 @@ def test_autograd_functions_match_oracle(gpu_lib):
     _theta_close(theta3.grad.numpy(), tb3)
 
 
+@pytest.mark.parametrize("k,kern", [(8, (1, 1.0, 0.1, 1e-4)), (32, (3, 1.0, 0.03, 1e-4))])
+def test_autograd_nll_fit_equals_nll(gpu_lib, k, kern):
+    """nll_fit (value and gradient from one pass) against nll (factor, value,
+    then the stored-factor gradient): the value to 1e-12, v's gradient to
+    1e-6, theta's to 1e-6 of its largest component; and against the
+    oracle's closed form at the stated 1e-4.  A cotangent of 2 scales both."""
+    from paper_2606_11402_gb300 import autograd as ga
+    N = 3000
+    g, f, want, fo, K = _setup(gpu_lib, "uniform", N, k, kern)
+    v = oracle.generate(fo, want["nbr_pos"], k, 64,
+                        workloads.white_noise(N, 73).astype(np.float64)).astype(np.float32)
+    grads = []
+    for fn in (ga.nll, ga.nll_fit):
+        theta = torch.tensor([kern[2], kern[1], kern[3]], dtype=torch.float64, requires_grad=True)
+        vt = to_gpu(v).requires_grad_(True)
+        loss = fn(g, kern[0], theta, vt)
+        (2.0 * loss).backward()
+        grads.append((loss.item(), np_(vt.grad), theta.grad.numpy()))
+    (l0, vb0, tb0), (l1, vb1, tb1) = grads
+    assert abs(l1 - l0) <= 1e-12 * abs(l0)
+    assert rel_norm(vb1, vb0) < 1e-6
+    assert np.all(np.abs(tb1 - tb0) <= 1e-6 * np.abs(tb0).max()), (tb1, tb0)
+    vbar_or, tb_or = oracle.nll_grad(want, K, v.astype(np.float64))
+    assert rel_norm(vb1, 2.0 * vbar_or) < 1e-4
+    _theta_close(tb1, 2.0 * tb_or)
+
+
 @pytest.mark.parametrize("case", CASES)
 def test_nll_point_gradient(gpu_lib, case):
     """dNLL/d(points) with the graph held fixed, against the oracle (itself
