@@ -14,9 +14,17 @@ value = points per second through one step (N / step time).
 e2e   = the same through the public API from pinned HOST buffers: xi copied
         in, v and xi and logdet copied out, inside the timed region.
 
-Multi-GPU: the path does not shard (one instance per GPU); under torchrun
-every rank runs an independent replica and value sums the ranks' points
-over the slowest rank's time ("replicas only", weak scaling).
+Beside the line: the graph build and factor rates, the on-the-fly sweeps,
+the adjoints (NLL gradient, generate VJP, the one-pass NLL value and
+gradient, the vector-only VJPs), the differentiation workload (N = 2^22,
+k = 32, SE), the large-dynamic-range and scale legs, the serving stream and
+the CPU oracle's per-stage baseline.
+
+Multi-GPU: the headline step contains generate, which does not shard (every
+depth level would need an exchange); under torchrun every rank runs an
+independent replica and value sums the ranks' points over the slowest
+rank's time (weak scaling).  The NLL and its gradient shard by position
+range (shard.py).
 
 --impl reference times the FP64 CPU oracle (the reference arm of this
 project) on a bounded sample of the same workload on the host cores.
