@@ -17,6 +17,9 @@
 //  * dense block (L0 = chol(K_00)): Lbar0 from the sweep, then
 //      Kbar_00 = L0^-T Phi(L0^T Lbar0) L0^-1 (Phi: lower triangle, halved
 //      diagonal), theta_bar += sum Kbar_00 dK_00/dtheta.
+//  * NLL value and gradient in one pass (graphgp_nll_grad_fused): per row the
+//      factor, xi_i, the value's terms, the whiten-VJP scatter and the
+//      factor backward above, each conditional computed once.
 // theta = (lengthscale, sigma2, nugget); theta_bar is accumulated in FP64.
 #include <algorithm>
 
