@@ -89,8 +89,8 @@ typedef struct {
 } graphgp_kernel;
 
 typedef struct {
-  int32_t n0;         /* size of the dense initial block (Sec. 2.2, Alg. 1
-                         line "dense initial batch"); 0 = default
+  int32_t n0;         /* size of the dense initial block (Sec. 2.2; the
+                         dense initial batch of Alg. 1); 0 = default
                          min(N, max(k, 256)) */
   int32_t split_rule; /* k-d split dimension: 0 = widest bounding-box extent
                          (ties to the lowest dimension), 1 = level mod 3

@@ -13,7 +13,7 @@ composes the steps in the paper's order:
   "Bit-reversed ordering";
 * preceding k-nearest neighbours -- Sec. 2.1, Sec. 2.2;
 * depth and depth-sorted order -- Sec. 2.2 "Batch construction";
-* factor -- Sec. 2.1 Eq. 2 (dense block: Alg. 1 first line);
+* factor -- Sec. 2.1 Eq. 2 (dense block: the dense initial batch of Alg. 1);
 * generate / whiten / logdet -- Alg. 1 and Sec. 3;
 * adjoints -- Sec. 2.3 (derivatives of the conditioning steps).
 

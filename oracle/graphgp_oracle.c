@@ -430,7 +430,7 @@ static int row_count(const int32_t* row, int k) {
  *   K_cc[a][b] = kappa(|x_a - x_b|) + nugget [a == b],  K_ci, K_ii = kappa(0)
  *   + nugget;  L = chol(K_cc);  y = L^-1 K_ci;  b = L^-T y;
  *   sigma^2 = K_ii - y.y;  sigma = sqrt(sigma^2).
- * Dense block (Alg. 1, first line): L0 = chol(K_00 + nugget I) over
+ * Dense block (the dense initial batch of Alg. 1): L0 = chol(K_00 + nugget I) over
  * positions 0..n0-1 and sigma_i = L0_ii.  logdet = 2 sum log sigma_i.
  * Distances are FP64 from the FP32 coordinates.                             */
 /* ------------------------------------------------------------------------ */

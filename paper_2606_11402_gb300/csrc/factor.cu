@@ -1,5 +1,6 @@
 // Per-point conditioning factors (Sec. 2.1 Eq. 2; Alg. 1) and the dense
-// initial block (Alg. 1, first line; Sec. 2.2 "Batch construction").
+// initial block (the dense initial batch of Alg. 1; Sec. 2.2 "Batch
+// construction").
 //
 // Per point i with c = c(i): b_i = K_ic K_cc^-1 and sigma_i^2 =
 // K_ii - K_ic K_cc^-1 K_ci.  A group of G lanes (G = 8, 16 or 32 >= k) of one

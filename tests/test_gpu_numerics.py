@@ -109,7 +109,7 @@ def test_factor_and_sweeps_several_tiles(gpu_lib, kind, k):
 
 
 def test_all_dense(gpu_lib):
-    """N = n0: the whole field is the dense block (Alg. 1 first line)."""
+    """N = n0: the whole field is the dense block (the dense initial batch of Alg. 1)."""
     pts = workloads.uniform_cube(300, 5)
     g, f, want, fo = _setup(gpu_lib, pts, 8, KERNELS["m32"], n0=300)
     _check_factor(gpu_lib, g, f, want, fo)
