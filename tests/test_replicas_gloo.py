@@ -85,3 +85,16 @@ def test_reference_arm_line_on_rank0():
     assert cb["sample"] == d["config"]["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
+
+
+def test_host_cpu_list_parsing_and_fallback():
+    """The end-to-end leg allocates its pinned buffers from the GPU's local
+    host cores: sysfs cpu lists parse to sets, and without a GPU (or where
+    the topology is not exposed) no affinity change is asked for."""
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench._cpulist("0-3,8,10-11\n") == {0, 1, 2, 3, 8, 10, 11}
+    assert bench._cpulist("5") == {5}
+    assert bench._cpulist("") == set()
+    if not torch.cuda.is_available():
+        assert bench._near_gpu_cpus(0) is None
